@@ -1,0 +1,205 @@
+/*
+ * gp.h -- C ABI of libgp: exact Gaussian-process inference by blackbox
+ * kernel-matrix products on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2109.09817 ("Molecular energy learning using alternative
+ * blackbox matrix-matrix multiplication algorithm for exact Gaussian
+ * process").  Problem statement (Sec. 2.2): data X in R^{N x d}, targets
+ * y in R^N, Gaussian noise sigma^2, kernel K : R^d x R^d -> R,
+ *   K-hat = K(X, X) + sigma^2 I,
+ *   E[f(X')]   = K(X', X) K-hat^{-1} y                        (Eq. pred)
+ *   L          = -1/2 y^T K-hat^{-1} y - 1/2 log|K-hat| - N/2 log 2 pi (Eq. ll)
+ * Kernel (Sec. 4): Matern 5/2, read with one lengthscale per feature (ARD):
+ *   r^2 = sum_j ((x_j - x'_j) / l_j)^2,
+ *   k(x, x') = s (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r).
+ *
+ * CONVENTIONS (all entry points)
+ *  - Every array argument is DEVICE memory on the context's device unless
+ *    the argument says "host".  The caller owns every array; the library
+ *    never frees or keeps caller pointers past the call.
+ *  - Feature matrices (X, X') are float32, row-major: point a's features at
+ *    X + a*d.
+ *  - A "block of t vectors of length n" is float32 COLUMN-MAJOR: vector c at
+ *    V + c*n, element a of it at V[c*n + a].
+ *  - Work is queued on the context's CUDA stream.  Calls that return host
+ *    values (ranks, iteration counts, scalars) synchronise that stream
+ *    before returning; the others are asynchronous.
+ *  - Return value: GP_OK or a negative-free error code below; the message
+ *    of the last error is gp_last_error(ctx).  Invalid sizes/pointers give
+ *    GP_EINVAL before any work is queued.
+ *  - Hyperparameters are natural positive values (l_j, s, sigma^2 > 0).
+ */
+#ifndef GP_H_
+#define GP_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GP_API __attribute__((visibility("default")))
+#else
+#define GP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes -------------------------------------------------------- */
+enum {
+  GP_OK = 0,
+  GP_EINVAL = 1,      /* bad argument (size, null pointer, value range)      */
+  GP_ENOMEM = 2,      /* device workspace allocation failed                  */
+  GP_ENOTCONV = 3,    /* CG hit max_iter before every column met tol; the
+                         outputs hold the last iterate and its residuals    */
+  GP_EBREAKDOWN = 4,  /* CG lost definiteness: d^T K-hat d <= 0 or r^T z <= 0 */
+  GP_ENONPD = 5,      /* pivoted Cholesky met a residual diagonal <= 0 before
+                         the requested rank (rank_out holds the rank reached) */
+  GP_ETIMEOUT = 6,    /* a bounded device-side wait gave up                  */
+  GP_ECUDA = 7        /* a CUDA runtime/driver call failed                   */
+};
+
+/* ---- arithmetic of the K-hat product ------------------------------------ */
+enum {
+  GP_FP32_PLAIN = 0,      /* FP32 FFMA on the CUDA cores only               */
+  GP_FP32_SPLIT_TF32 = 1, /* tcgen05 kind::tf32, hi+lo split operands
+                             (3 products) for both the cross term X X^T and
+                             the contraction K V: FP32-class accuracy       */
+  GP_BF16_SPLIT = 2,      /* tcgen05 kind::f16 (bf16) hi+lo split, both
+                             contractions                                   */
+  GP_TF32 = 3,            /* tcgen05 kind::tf32, single-pass operands       */
+  GP_BF16 = 4             /* tcgen05 kind::f16 (bf16), single-pass          */
+};
+
+/* posterior variance modes of gp_predict */
+enum { GP_VAR_NONE = 0, GP_VAR_EXACT = 1 };
+
+typedef struct gp_ctx gp_ctx;
+typedef struct gp_model gp_model;
+
+/* Hyperparameters theta = (l, s, sigma^2).  lengthscale: HOST pointer to d
+ * doubles, read during the call only. */
+typedef struct {
+  const double* lengthscale;
+  double outputscale;
+  double sigma2;
+} gp_theta;
+
+/* Solver diagnostics (host struct, filled when a pointer is passed). */
+typedef struct {
+  int iters_max;        /* CG steps taken (max over columns)                */
+  int iters_y;          /* steps taken by column 0 (the y column)           */
+  int rank;             /* preconditioner rank reached                      */
+  int n_kmatmul;        /* K-hat products issued                            */
+  double relres_y;      /* CG recurrence residual ||r||/||b|| of column 0   */
+  double relres_max;    /* max over columns                                  */
+  double logdet_P;      /* log|P|, P = L L^T + sigma^2 I                    */
+  double yKinvy;        /* y^T K-hat^{-1} y                                  */
+} gp_stats;
+
+/* ---- context -------------------------------------------------------------
+ * gp_create: bind a context to CUDA device `device` and stream `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  The context owns a
+ * device workspace that grows on demand and is freed by gp_destroy.  One
+ * context per stream; a context is not thread-safe. */
+GP_API int gp_create(gp_ctx** out, int device, void* stream);
+GP_API void gp_destroy(gp_ctx* ctx);
+GP_API int gp_set_stream(gp_ctx* ctx, void* stream);
+GP_API int gp_sync(gp_ctx* ctx);
+GP_API const char* gp_last_error(const gp_ctx* ctx);
+/* Number of kernels this context has launched (diagnostics). */
+GP_API int64_t gp_launch_count(const gp_ctx* ctx);
+/* K-hat V timing: gp_profile(ctx, 1) resets the counters and records a CUDA
+ * event pair on the context's stream around every K-hat V product issued
+ * from then on (gp_profile(ctx, 0) stops recording).  gp_profile_read
+ * synchronises and returns (HOST outputs) the number of products, their
+ * summed device time in ms, their GEMM-equivalent flops 2 m n (d + t) and
+ * their kernel entries m n (m, n = rows and columns of the K tile grid). */
+GP_API int gp_profile(gp_ctx* ctx, int enable);
+GP_API int gp_profile_read(gp_ctx* ctx, int64_t* products, double* ms,
+                           double* flops, double* entries);
+
+/* ---- K-hat V (Sec. 3.1 "only the matrix-vector multiplications"; Sec. 3.2
+ * "O(N) memory"; Sec. 4 kernel tiles) --------------------------------------
+ * out = (K(X, X) + sigma^2 I) V, with K formed tile by tile from X and
+ * never stored.  X: N x d row-major.  V, out: t vectors of length N,
+ * column-major.  1 <= t <= 512.  `precision` is one of GP_FP32_PLAIN ...
+ * GP_BF16.  out must not alias V. */
+GP_API int gp_kmatmul(gp_ctx* ctx, const float* X, int64_t N, int d,
+               const gp_theta* theta, const float* V, int t, float* out,
+               int precision);
+
+/* out = K(X', X) V (the cross covariance of Eq. pred).  X': M x d, X: N x d,
+ * V: t vectors of length N, out: t vectors of length M. */
+GP_API int gp_kcross_matmul(gp_ctx* ctx, const float* Xp, int64_t M, const float* X,
+                     int64_t N, int d, const gp_theta* theta, const float* V,
+                     int t, float* out, int precision);
+
+/* ---- pivoted Cholesky preconditioner (Sec. 3.2, rank-k greedy factor) ----
+ * Greedy rank-k factor K ~ L L^T in FP64: at step j the pivot is the row
+ * with the largest residual diagonal (lowest index on ties), the column is
+ * (K(X, x_p) - L_{:,<j} L_{p,<j}^T) / sqrt(d_p), and the pivot's residual
+ * is set to zero.  Stops early when the largest residual diagonal is
+ * <= 1e-12 s.  L: N x k FP64 column-major (column j at L + j*N); columns
+ * past the rank reached are zero.  piv: k int64 (past the rank: -1).
+ * rank_out: HOST int.  Synchronises. */
+GP_API int gp_pivchol(gp_ctx* ctx, const float* X, int64_t N, int d,
+               const gp_theta* theta, int k, double* L, int64_t* piv,
+               int* rank_out);
+
+/* ---- mBCG (Sec. 3.2; CG of Sec. 3.1 with preconditioner P) ----------------
+ * Solves K-hat Omega = B for t right-hand sides at once with preconditioned
+ * CG, P = L L^T + sigma^2 I applied by the Woodbury identity (L from
+ * gp_pivchol, rank k; k = 0 means P = sigma^2 I, i.e. plain CG).  Every
+ * column shares each K-hat product.  Column c stops (is frozen) once
+ * ||r_c|| / ||b_c|| < tol (Sec. 4 stop rule); the solve stops when all
+ * columns stopped or after max_iter steps (then GP_ENOTCONV).
+ * B, Omega: t vectors of length N (column-major).  alpha_hist, beta_hist:
+ * nullable device FP64 arrays of max_iter*t, entry [j*t + c] = the CG
+ * coefficient of column c at step j (0 after the column stopped); the
+ * Lanczos tridiagonal of column c follows from its first iters[c] entries.
+ * iters, rel_resid: nullable HOST arrays of t.  Synchronises. */
+GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
+            const gp_theta* theta, const double* L, int k, const float* B,
+            int t, double tol, int max_iter, int precision, float* Omega,
+            double* alpha_hist, double* beta_hist, int* iters,
+            double* rel_resid);
+
+/* ---- log marginal likelihood and gradient (Eq. ll; Sec. 3.2) -------------
+ * One pass of the whole training path: rank-k pivoted Cholesky; probes
+ * z_c = L e1_c + sigma e2_c (c < n_probes) with Rademacher signs from the
+ * SplitMix64 sequence seeded by `seed`; mBCG on [y | z_1..z_t]; Lanczos
+ * quadrature of log|K-hat|; and the gradient
+ *   dL/dtheta = 1/2 a^T dK a - 1/(2t) sum_c (K-hat^{-1} z_c)^T dK (P^{-1} z_c)
+ * with a = K-hat^{-1} y.  y: N floats (device).  Outputs are HOST:
+ * logml, logdet, logdet_stderr (standard error over probes, nullable),
+ * grad (d + 2 doubles: dL/dl_1..dL/dl_d, dL/ds, dL/dsigma^2; nullable to
+ * skip the gradient pass), stats (nullable).  1 <= n_probes <= 255.
+ * Synchronises. */
+GP_API int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
+                      const gp_theta* theta, const float* y, int n_probes,
+                      uint64_t seed, int k, double tol, int max_iter,
+                      int precision, double* logml, double* logdet,
+                      double* grad, double* logdet_stderr, gp_stats* stats);
+
+/* ---- trained model and prediction (Eq. pred) ------------------------------
+ * gp_model_fit keeps, on the device, the prepared features, a = K-hat^{-1} y
+ * (mBCG to `tol`), the preconditioner factor and the hyperparameters.
+ * X and y are copied; the caller may free them afterwards.  Synchronises. */
+GP_API int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
+                 const gp_theta* theta, const float* y, int k, double tol,
+                 int max_iter, int precision, gp_model** out,
+                 gp_stats* stats);
+GP_API void gp_model_free(gp_model* model);
+
+/* mean = K(X', X) a.  var (nullable): var_mode GP_VAR_EXACT gives the latent
+ * posterior variance k(x', x') - k*^T K-hat^{-1} k* (Eq. pred read as the
+ * standard posterior variance) by an mBCG solve with the M columns k* as
+ * right-hand sides (to the model's tol).  Xp: M x d row-major; mean, var: M
+ * floats.  Synchronises when var is requested. */
+GP_API int gp_predict(gp_ctx* ctx, const gp_model* model, const float* Xp, int64_t M,
+               float* mean, float* var, int var_mode);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H_ */

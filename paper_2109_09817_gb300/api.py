@@ -1,0 +1,247 @@
+"""Python binding of libgp with the C ABI's names (argument marshalling only).
+
+Every step of the path runs in libgp's CUDA kernels; this module only turns
+torch device tensors into pointers and sizes and raises on error codes.
+PyTorch supplies device memory and the stream.
+
+Layouts (as in include/gp.h): features X are (N, d) float32 row-major; a
+block of t vectors of length N is a (t, N) float32 tensor (row c = vector c).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (GP_BF16, GP_BF16_SPLIT, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
+                   GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_OK, GP_ENOTCONV,
+                   GP_EBREAKDOWN, ERROR_NAMES)
+
+PRECISIONS = {"fp32": GP_FP32_PLAIN, "split_tf32": GP_FP32_SPLIT_TF32,
+              "split_bf16": GP_BF16_SPLIT, "tf32": GP_TF32, "bf16": GP_BF16}
+
+
+class GPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+@dataclasses.dataclass
+class Theta:
+    """Hyperparameters (natural, positive): lengthscale (d,), s, sigma^2."""
+    lengthscale: np.ndarray
+    outputscale: float = 1.0
+    sigma2: float = 1e-4
+
+    def as_c(self):
+        ell = np.ascontiguousarray(self.lengthscale, dtype=np.float64)
+        th = _lib.GpTheta(ell.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          float(self.outputscale), float(self.sigma2))
+        return th, ell  # keep `ell` alive for the call
+
+
+class Context:
+    """A libgp context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        self.lib = _lib.load()
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        rc = self.lib.gp_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != GP_OK:
+            raise GPError(rc, "gp_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def check(self, rc: int, allow=()):
+        if rc != GP_OK and rc not in allow:
+            raise GPError(rc, self.lib.gp_last_error(self.h).decode())
+        return rc
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.gp_launch_count(self.h))
+
+    def sync(self):
+        self.check(self.lib.gp_sync(self.h))
+
+
+def _p(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dev(ctx: Context, t: torch.Tensor, dtype, name: str):
+    if not (t.is_cuda and t.device.index == ctx.device):
+        raise ValueError(f"{name} must be on cuda:{ctx.device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _block(ctx, V, N, name):
+    if V.dim() == 1:
+        V = V.view(1, -1)
+    _dev(ctx, V, torch.float32, name)
+    if V.shape[1] != N:
+        raise ValueError(f"{name} must be (t, {N})")
+    return V
+
+
+def gp_kmatmul(ctx: Context, X: torch.Tensor, theta: Theta, V: torch.Tensor,
+               precision: int = GP_FP32_PLAIN, out: Optional[torch.Tensor] = None):
+    """(K(X,X) + sigma^2 I) V; V and the result are (t, N)."""
+    _dev(ctx, X, torch.float32, "X")
+    N, d = X.shape
+    V = _block(ctx, V, N, "V")
+    out = torch.empty_like(V) if out is None else out
+    th, keep = theta.as_c()
+    ctx.check(ctx.lib.gp_kmatmul(ctx.h, _p(X), N, d, ctypes.byref(th), _p(V), V.shape[0],
+                                 _p(out), precision))
+    return out
+
+
+def gp_kcross_matmul(ctx: Context, Xp: torch.Tensor, X: torch.Tensor, theta: Theta,
+                     V: torch.Tensor, precision: int = GP_FP32_PLAIN):
+    """K(X', X) V; V is (t, N), the result (t, M)."""
+    _dev(ctx, X, torch.float32, "X")
+    _dev(ctx, Xp, torch.float32, "Xp")
+    N, d = X.shape
+    M = Xp.shape[0]
+    V = _block(ctx, V, N, "V")
+    out = torch.empty((V.shape[0], M), dtype=torch.float32, device=X.device)
+    th, keep = theta.as_c()
+    ctx.check(ctx.lib.gp_kcross_matmul(ctx.h, _p(Xp), M, _p(X), N, d, ctypes.byref(th),
+                                       _p(V), V.shape[0], _p(out), precision))
+    return out
+
+
+def gp_pivchol(ctx: Context, X: torch.Tensor, theta: Theta, k: int):
+    """Rank-k pivoted Cholesky (FP64).  Returns (L (k, N) float64, piv (k,), rank)."""
+    _dev(ctx, X, torch.float32, "X")
+    N, d = X.shape
+    L = torch.empty((max(k, 1), N), dtype=torch.float64, device=X.device)
+    piv = torch.empty(max(k, 1), dtype=torch.int64, device=X.device)
+    rank = ctypes.c_int(0)
+    th, keep = theta.as_c()
+    ctx.check(ctx.lib.gp_pivchol(ctx.h, _p(X), N, d, ctypes.byref(th), k, _p(L), _p(piv),
+                                 ctypes.byref(rank)))
+    return L[:k], piv[:k], rank.value
+
+
+def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tensor],
+            B: torch.Tensor, tol: float = 1e-6, max_iter: int = 1000,
+            precision: int = GP_FP32_PLAIN, allow_notconv: bool = True):
+    """Batched PCG on K-hat Omega = B; returns dict(Omega, alpha, beta, iters,
+    relres, rc).  L: (k, N) float64 from gp_pivchol or None."""
+    _dev(ctx, X, torch.float32, "X")
+    N, d = X.shape
+    B = _block(ctx, B, N, "B")
+    t = B.shape[0]
+    k = 0 if L is None else L.shape[0]
+    if L is not None:
+        _dev(ctx, L, torch.float64, "L")
+    Om = torch.empty_like(B)
+    ah = torch.zeros((max_iter, t), dtype=torch.float64, device=X.device)
+    bh = torch.zeros((max_iter, t), dtype=torch.float64, device=X.device)
+    iters = (ctypes.c_int * t)()
+    rr = (ctypes.c_double * t)()
+    th, keep = theta.as_c()
+    allow = (GP_ENOTCONV,) if allow_notconv else ()
+    rc = ctx.check(ctx.lib.gp_mbcg(ctx.h, _p(X), N, d, ctypes.byref(th), _p(L), k, _p(B), t,
+                                   tol, max_iter, precision, _p(Om), _p(ah), _p(bh), iters, rr),
+                   allow=allow)
+    return dict(Omega=Om, alpha=ah, beta=bh, iters=np.array(iters[:]),
+                relres=np.array(rr[:]), rc=rc)
+
+
+def gp_logml_and_grad(ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tensor,
+                      n_probes: int = 15, seed: int = 0, k: int = 32, tol: float = 1e-6,
+                      max_iter: int = 1000, precision: int = GP_FP32_PLAIN,
+                      want_grad: bool = True, allow_notconv: bool = False):
+    """Eq. (ll) and its gradient (natural parameters l_1..l_d, s, sigma^2)."""
+    _dev(ctx, X, torch.float32, "X")
+    _dev(ctx, y, torch.float32, "y")
+    N, d = X.shape
+    logml = ctypes.c_double()
+    logdet = ctypes.c_double()
+    se = ctypes.c_double()
+    grad = (ctypes.c_double * (d + 2))()
+    stats = _lib.GpStats()
+    th, keep = theta.as_c()
+    allow = (GP_ENOTCONV,) if allow_notconv else ()
+    rc = ctx.check(ctx.lib.gp_logml_and_grad(
+        ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), n_probes, ctypes.c_uint64(seed), k, tol,
+        max_iter, precision, ctypes.byref(logml), ctypes.byref(logdet),
+        grad if want_grad else None, ctypes.byref(se), ctypes.byref(stats)), allow=allow)
+    return dict(logml=logml.value, logdet=logdet.value, logdet_stderr=se.value,
+                grad=np.array(grad[:]) if want_grad else None, stats=stats.as_dict(), rc=rc)
+
+
+class Model:
+    """A fitted model resident on the device (gp_model_fit / gp_predict)."""
+
+    def __init__(self, ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tensor,
+                 k: int = 32, tol: float = 1e-6, max_iter: int = 1000,
+                 precision: int = GP_FP32_PLAIN):
+        _dev(ctx, X, torch.float32, "X")
+        _dev(ctx, y, torch.float32, "y")
+        self.ctx = ctx
+        N, d = X.shape
+        self.N, self.d = N, d
+        h = ctypes.c_void_p()
+        stats = _lib.GpStats()
+        th, keep = theta.as_c()
+        ctx.check(ctx.lib.gp_model_fit(ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), k, tol,
+                                       max_iter, precision, ctypes.byref(h), ctypes.byref(stats)))
+        self.h = h
+        self.stats = stats.as_dict()
+
+    def free(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.gp_model_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def gp_model_fit(ctx: Context, X, theta, y, k=32, tol=1e-6, max_iter=1000,
+                 precision=GP_FP32_PLAIN) -> Model:
+    return Model(ctx, X, theta, y, k, tol, max_iter, precision)
+
+
+def gp_predict(ctx: Context, model: Model, Xp: torch.Tensor, var_mode: int = GP_VAR_NONE):
+    """Predictive mean (and latent variance with GP_VAR_EXACT), Eq. (pred)."""
+    _dev(ctx, Xp, torch.float32, "Xp")
+    M = Xp.shape[0]
+    mean = torch.empty(M, dtype=torch.float32, device=Xp.device)
+    var = torch.empty(M, dtype=torch.float32, device=Xp.device) if var_mode else None
+    ctx.check(ctx.lib.gp_predict(ctx.h, model.h, _p(Xp), M, _p(mean), _p(var), var_mode))
+    return mean, var

@@ -1,0 +1,518 @@
+// mBCG (A6): batched preconditioned CG with FP64 scalar recurrences.
+//
+// arXiv 2109.09817 Sec. 3.1 (CG; preconditioner P; relative residual
+// ||K-hat w - y|| / ||y||), Sec. 3.2 (mBCG of ref. gardner2018gpytorch: t
+// independent PCG solves sharing each K-hat product, whose coefficients give
+// the Lanczos tridiagonals), Sec. 4 (stop when every relative residual is
+// below the tolerance).  Per column c and step j:
+//   W = K-hat D;  alpha = (r.z)/(d.w);  U += alpha D;  R -= alpha W;
+//   stop column if ||R_c||/||B_c|| < tol;  Z = P^{-1} R;
+//   beta = (r'.z')/(r.z);  D = Z + beta D.
+// The t-vector blocks are FP32 column-major (ld = padded N); every dot
+// product accumulates in FP64 with a fixed-order two-stage reduction, so a
+// column's result does not depend on which other columns share the solve.
+#include <algorithm>
+#include <cmath>
+
+#include "gp_internal.cuh"
+
+namespace gp {
+namespace {
+
+constexpr int kRedBlocks = 128;   // row chunks of the two-stage reductions
+
+struct CgScal {
+  double rz, rz_new, dw, bnorm, relres, alpha, beta;
+  int active, iters;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+  return s;   // valid in thread 0
+}
+
+// part[c * nblk + b] = sum over rows of block b of A_c . B_c (FP64)
+__global__ void dot_partial_kernel(const float* __restrict__ A,
+                                   const float* __restrict__ B, int64_t ld,
+                                   int64_t n, const CgScal* __restrict__ sc,
+                                   double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int c = blockIdx.y, nblk = gridDim.x;
+  if (sc && !sc[c].active) {
+    if (threadIdx.x == 0) part[(int64_t)c * nblk + blockIdx.x] = 0.0;
+    return;
+  }
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  const float* a = A + (int64_t)c * ld;
+  const float* b = B + (int64_t)c * ld;
+  double acc = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) acc += (double)a[i] * (double)b[i];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(int64_t)c * nblk + blockIdx.x] = s;
+}
+
+__global__ void sum_parts_kernel(const double* __restrict__ part, int nblk, int t,
+                                 double* __restrict__ out) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)c * nblk + b];
+    out[c] = s;
+  }
+}
+
+__global__ void copy_kernel(const float* __restrict__ src, int64_t lds,
+                            float* __restrict__ dst, int64_t ldd, int64_t n,
+                            int t, float scale) {
+  const int64_t total = n * t;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / n, a = i % n;
+    dst[c * ldd + a] = src ? scale * src[c * lds + a] : 0.f;
+  }
+}
+
+// ---- preconditioner P^{-1} = (I - L (sigma2 I + L^T L)^{-1} L^T) / sigma2 --
+// G partials: part[b][j * t + c] = sum_{a in chunk b} L32[j][a] R[c][a]
+__global__ void ltr_partial_kernel(const float* __restrict__ L32, int64_t ldl,
+                                   int k, const float* __restrict__ R, int64_t ldr,
+                                   int t, int64_t n, const CgScal* __restrict__ sc,
+                                   double* __restrict__ part) {
+  __shared__ float sL[64][65];
+  __shared__ float sR[64][65];
+  const int nblk = gridDim.x;
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  // this block covers pairs (j, c) with j in [j0, j0+64), c in [c0, c0+64)
+  const int j0 = blockIdx.y * 64, c0 = blockIdx.z * 64;
+  const int nj = min(64, k - j0), ncol = min(64, t - c0);
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int64_t rb = r0; rb < r1; rb += 64) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+      const int jj = idx / 64, rr = idx % 64;
+      const int64_t row = rb + rr;
+      sL[jj][rr] = (jj < nj && row < r1) ? L32[(int64_t)(j0 + jj) * ldl + row] : 0.f;
+      const bool act = jj < ncol && (!sc || sc[c0 + jj].active);
+      sR[jj][rr] = (act && row < r1) ? R[(int64_t)(c0 + jj) * ldr + row] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int pidx = threadIdx.x + q * 256;
+      const int jj = pidx / 64, cc = pidx % 64;
+      float a = 0.f;
+#pragma unroll 8
+      for (int rr = 0; rr < 64; ++rr) a = fmaf(sL[jj][rr], sR[cc][rr], a);
+      acc[q] += (double)a;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int pidx = threadIdx.x + q * 256;
+    const int jj = pidx / 64, cc = pidx % 64;
+    if (jj < nj && cc < ncol)
+      part[(int64_t)blockIdx.x * k * t + (int64_t)(j0 + jj) * t + (c0 + cc)] = acc[q];
+  }
+}
+
+// G[j][c] = sum over row blocks of the partials (fixed order); one thread
+// per (j, c), frozen columns skipped.
+__global__ void g_reduce_kernel(const double* __restrict__ part, int nblk, int k,
+                                int t, const CgScal* __restrict__ sc,
+                                double* __restrict__ G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * t) return;
+  const int c = idx % t;
+  if (sc && !sc[c].active) {
+    G[idx] = 0.0;
+    return;
+  }
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * k * t + idx];
+  G[idx] = s;
+}
+
+// w = C^{-1} G (C = sigma2 I + L^T L, inverse precomputed in FP64); wf k x t.
+__global__ void w_apply_kernel(const double* __restrict__ Cinv,
+                               const double* __restrict__ G, int k, int t,
+                               float* __restrict__ wf) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * t) return;
+  const int j = idx / t, c = idx % t;
+  double s = 0.0;
+  for (int i = 0; i < k; ++i) s += Cinv[(int64_t)i * k + j] * G[(int64_t)i * t + c];
+  wf[idx] = (float)s;
+}
+
+// Z_c = (R_c - L32 w_c) / sigma2 on 32-column chunks; rz partials.
+__global__ void z_apply_kernel(const float* __restrict__ L32, int64_t ldl, int k,
+                               const float* __restrict__ wf, int t,
+                               const float* __restrict__ R, float* __restrict__ Z,
+                               int64_t ld, int64_t n, float inv_s2,
+                               const CgScal* __restrict__ sc,
+                               double* __restrict__ rzpart) {
+  extern __shared__ float sw[];   // k x 32 chunk of w
+  __shared__ double sh[32];
+  const int c0 = blockIdx.y * 32;
+  const int nc = min(32, t - c0);
+  for (int idx = threadIdx.x; idx < k * 32; idx += blockDim.x) {
+    const int j = idx / 32, cc = idx % 32;
+    sw[idx] = cc < nc ? wf[j * t + c0 + cc] : 0.f;
+  }
+  __syncthreads();
+  bool act[32];
+#pragma unroll
+  for (int cc = 0; cc < 32; ++cc) act[cc] = cc < nc && (!sc || sc[c0 + cc].active);
+  const int nblk = gridDim.x;
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  double rz[32];
+#pragma unroll
+  for (int cc = 0; cc < 32; ++cc) rz[cc] = 0.0;
+  for (int64_t a = r0 + threadIdx.x; a < r1; a += blockDim.x) {
+    float acc[32];
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) acc[cc] = 0.f;
+    for (int j = 0; j < k; ++j) {
+      const float l = L32[(int64_t)j * ldl + a];
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) acc[cc] = fmaf(l, sw[j * 32 + cc], acc[cc]);
+    }
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) {
+      if (!act[cc]) continue;
+      const int64_t o = (int64_t)(c0 + cc) * ld + a;
+      const float r = R[o];
+      const float z = (r - acc[cc]) * inv_s2;
+      Z[o] = z;
+      rz[cc] += (double)r * (double)z;
+    }
+  }
+  if (rzpart) {
+    for (int cc = 0; cc < nc; ++cc) {
+      const double s = block_sum(rz[cc], sh);
+      if (threadIdx.x == 0) rzpart[(int64_t)(c0 + cc) * nblk + blockIdx.x] = s;
+    }
+  }
+}
+
+// ---- CG scalar kernels -------------------------------------------------------
+__global__ void cg_init_kernel(CgScal* sc, const double* __restrict__ bb,
+                               const double* __restrict__ rzpart, int nblk, int t,
+                               double* __restrict__ rz0, int* iters,
+                               double* relres, int* nact) {
+  if (threadIdx.x == 0) *nact = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    double rz = 0.0;
+    for (int b = 0; b < nblk; ++b) rz += rzpart[(int64_t)c * nblk + b];
+    CgScal s;
+    s.bnorm = sqrt(bb[c]);
+    s.rz = rz;
+    s.rz_new = rz;
+    s.dw = 0.0;
+    s.alpha = 0.0;
+    s.beta = 0.0;
+    s.active = s.bnorm > 0.0 ? 1 : 0;
+    s.relres = s.active ? 1.0 : 0.0;
+    s.iters = 0;
+    sc[c] = s;
+    if (rz0) rz0[c] = rz;
+    if (iters) iters[c] = 0;
+    if (relres) relres[c] = s.relres;
+    if (s.active) atomicAdd(nact, 1);
+  }
+}
+
+__global__ void cg_alpha_kernel(CgScal* sc, const double* __restrict__ dwpart,
+                                int nblk, int t, int it, double* __restrict__ ah,
+                                int* flags) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    CgScal s = sc[c];
+    double a = 0.0;
+    if (s.active) {
+      double dw = 0.0;
+      for (int b = 0; b < nblk; ++b) dw += dwpart[(int64_t)c * nblk + b];
+      s.dw = dw;
+      if (!(dw > 0.0) || !(s.rz > 0.0) || !isfinite(dw)) {
+        atomicOr(flags + 1, 1);   // breakdown
+        s.active = 0;
+      } else {
+        a = s.rz / dw;
+      }
+    }
+    s.alpha = a;
+    sc[c] = s;
+    ah[(int64_t)it * t + c] = a;
+  }
+}
+
+// U += alpha D, R -= alpha W for active columns; ||R||^2 partials.
+__global__ void cg_update_kernel(float* __restrict__ U, float* __restrict__ R,
+                                 const float* __restrict__ D,
+                                 const float* __restrict__ W, int64_t ld,
+                                 int64_t ldu, int64_t n,
+                                 const CgScal* __restrict__ sc,
+                                 double* __restrict__ rrpart) {
+  __shared__ double sh[32];
+  const int c = blockIdx.y, nblk = gridDim.x;
+  const CgScal s = sc[c];
+  if (!s.active) {
+    if (threadIdx.x == 0) rrpart[(int64_t)c * nblk + blockIdx.x] = 0.0;
+    return;
+  }
+  const float a = (float)s.alpha;
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  float* u = U + (int64_t)c * ldu;
+  float* r = R + (int64_t)c * ld;
+  const float* dd = D + (int64_t)c * ld;
+  const float* w = W + (int64_t)c * ld;
+  double acc = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    u[i] = fmaf(a, dd[i], u[i]);
+    const float rn = fmaf(-a, w[i], r[i]);
+    r[i] = rn;
+    acc += (double)rn * (double)rn;
+  }
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) rrpart[(int64_t)c * nblk + blockIdx.x] = tot;
+}
+
+__global__ void cg_check_beta_kernel(CgScal* sc, const double* __restrict__ rrpart,
+                                     const double* __restrict__ rzpart, int nblk,
+                                     int t, int it, double tol,
+                                     double* __restrict__ bh, int* iters,
+                                     double* relres, int* flags) {
+  if (threadIdx.x == 0) flags[0] = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    CgScal s = sc[c];
+    double b = 0.0;
+    if (s.active) {
+      double rr = 0.0, rz = 0.0;
+      for (int q = 0; q < nblk; ++q) {
+        rr += rrpart[(int64_t)c * nblk + q];
+        rz += rzpart[(int64_t)c * nblk + q];
+      }
+      s.relres = sqrt(rr) / s.bnorm;
+      s.iters = it + 1;
+      if (s.relres < tol) {
+        s.active = 0;
+      } else if (!(rz > 0.0) || !isfinite(rz)) {
+        atomicOr(flags + 1, 1);
+        s.active = 0;
+      } else {
+        b = rz / s.rz;
+        s.rz = rz;
+      }
+      if (iters) iters[c] = s.iters;
+      if (relres) relres[c] = s.relres;
+    }
+    s.beta = b;
+    sc[c] = s;
+    bh[(int64_t)it * t + c] = b;
+    if (s.active) atomicAdd(flags, 1);
+  }
+}
+
+__global__ void cg_dupdate_kernel(float* __restrict__ D, const float* __restrict__ Z,
+                                  int64_t ld, int64_t n, const CgScal* __restrict__ sc) {
+  const int c = blockIdx.y;
+  const CgScal s = sc[c];
+  if (!s.active) return;
+  const float b = (float)s.beta;
+  float* dd = D + (int64_t)c * ld;
+  const float* z = Z + (int64_t)c * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dd[i] = fmaf(b, dd[i], z[i]);
+}
+
+// ---- probes: z_c = L e1_c + sigma e2_c, SplitMix64 Rademacher signs ----------
+__device__ __forceinline__ float splitmix_sign(uint64_t seed, uint64_t ctr) {
+  uint64_t z = seed + (ctr + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z = z ^ (z >> 31);
+  return (z >> 63) ? -1.f : 1.f;
+}
+
+__global__ void probe_kernel(const double* __restrict__ L, int64_t n, int k,
+                             double sigma, uint64_t seed, int np,
+                             float* __restrict__ Z, int64_t ldz) {
+  extern __shared__ float se1[];   // k x np
+  for (int idx = threadIdx.x; idx < k * np; idx += blockDim.x) {
+    const int i = idx / np, c = idx % np;
+    const uint64_t ctr = (1ULL << 56) | ((uint64_t)c << 32) | (uint64_t)i;
+    se1[idx] = splitmix_sign(seed, ctr);
+  }
+  __syncthreads();
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    for (int c = 0; c < np; ++c) {
+      double z = sigma * (double)splitmix_sign(seed, ((uint64_t)c << 32) | (uint64_t)a);
+      for (int i = 0; i < k; ++i) z += L[(int64_t)i * n + a] * (double)se1[i * np + c];
+      Z[(int64_t)c * ldz + a] = (float)z;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int copy_vectors(gp_ctx* ctx, const float* src, int64_t lds, float* dst,
+                 int64_t ldd, int64_t n, int t, float scale) {
+  const int64_t total = n * t;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 16LL * ctx->num_sms));
+  copy_kernel<<<g, 256, 0, ctx->stream>>>(src, lds, dst, ldd, n, t, scale);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+int dot_columns(gp_ctx* ctx, const float* A, const float* B, int64_t ld,
+                int64_t n, int t, double* out) {
+  double* part = ws<double>(ctx, WS_PART, (size_t)kRedBlocks * t);
+  if (!part) return set_err(ctx, GP_ENOMEM, "workspace (dot)");
+  dot_partial_kernel<<<dim3(kRedBlocks, t), 256, 0, ctx->stream>>>(A, B, ld, n, nullptr, part);
+  GP_LAUNCHED(ctx);
+  sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(part, kRedBlocks, t, out);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+int probe_vectors(gp_ctx* ctx, const double* L, int64_t n, int k, double sigma,
+                  uint64_t seed, int n_probes, float* Z, int64_t ldz) {
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms));
+  const size_t shm = sizeof(float) * (size_t)std::max(1, k * n_probes);
+  if (shm > 48 * 1024)
+    GP_CUDA(ctx, cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  probe_kernel<<<g, 256, shm, ctx->stream>>>(L, n, k, sigma, seed, n_probes, Z, ldz);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
+                              const float* R, float* Z, int64_t ld, int t,
+                              const CgScal* sc, double* rzpart) {
+  const int k = pc ? pc->k : 0;
+  const double sigma2 = pc ? pc->sigma2 : 1.0;
+  float* wf = nullptr;
+  if (k > 0) {
+    const int nb = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 256)));
+    double* part = ws<double>(ctx, WS_CG_G, (size_t)nb * k * t + (size_t)k * t);
+    wf = ws<float>(ctx, WS_LZ_OUT, (size_t)k * t);
+    double* G = part + (size_t)nb * k * t;
+    if (!part || !wf) return set_err(ctx, GP_ENOMEM, "workspace (precond)");
+    dim3 grid(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 64));
+    ltr_partial_kernel<<<grid, 256, 0, ctx->stream>>>(pc->L32, pc->ld32, k, R, ld, t, n, sc, part);
+    GP_LAUNCHED(ctx);
+    const unsigned g2 = (unsigned)ceil_div((int64_t)k * t, 128);
+    g_reduce_kernel<<<g2, 128, 0, ctx->stream>>>(part, nb, k, t, sc, G);
+    GP_LAUNCHED(ctx);
+    w_apply_kernel<<<g2, 128, 0, ctx->stream>>>(pc->cinv, G, k, t, wf);
+    GP_LAUNCHED(ctx);
+  }
+  const size_t shm = sizeof(float) * (size_t)std::max(1, k) * 32;
+  if (shm > 48 * 1024)
+    GP_CUDA(ctx, cudaFuncSetAttribute(z_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  dim3 grid(kRedBlocks, (unsigned)ceil_div(t, 32));
+  z_apply_kernel<<<grid, 256, shm, ctx->stream>>>(pc ? pc->L32 : nullptr, pc ? pc->ld32 : 0, k, wf, t,
+                                                  R, Z, ld, n, (float)(1.0 / sigma2), sc, rzpart);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+int precond_apply(gp_ctx* ctx, const Precond* pc, int64_t n, const float* R,
+                  float* Z, int64_t ld, int t, const int* active, double* rz_out) {
+  (void)active;
+  double* part = nullptr;
+  if (rz_out) {
+    part = ws<double>(ctx, WS_PART, (size_t)kRedBlocks * t);
+    if (!part) return set_err(ctx, GP_ENOMEM, "workspace (precond rz)");
+  }
+  GP_TRY(precond_apply_impl(ctx, pc, n, R, Z, ld, t, nullptr, part));
+  if (rz_out) {
+    sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(part, kRedBlocks, t, rz_out);
+    GP_LAUNCHED(ctx);
+  }
+  return GP_OK;
+}
+
+int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res) {
+  const Prep& p = *a.prep;
+  const int64_t n = p.n, ld = p.n_pad;
+  const int t = a.t;
+  float* R = ws<float>(ctx, WS_CG_R, (size_t)ld * t);
+  float* Z = ws<float>(ctx, WS_CG_Z, (size_t)ld * t);
+  float* D = ws<float>(ctx, WS_CG_D, (size_t)ld * t);
+  float* W = ws<float>(ctx, WS_CG_W, (size_t)ld * t);
+  CgScal* sc = static_cast<CgScal*>(ws_get(ctx, WS_CG_SCAL, sizeof(CgScal) * t + 64));
+  double* part = ws<double>(ctx, WS_CG_PART, (size_t)3 * kRedBlocks * t + t);
+  int* flags = static_cast<int*>(pinned_get(ctx, 64));
+  if (!R || !Z || !D || !W || !sc || !part || !flags)
+    return set_err(ctx, GP_ENOMEM, "workspace (mbcg)");
+  int* dflags = reinterpret_cast<int*>(reinterpret_cast<char*>(sc) + sizeof(CgScal) * t);
+  double* p_dw = part;
+  double* p_rr = part + (size_t)kRedBlocks * t;
+  double* p_rz = part + (size_t)2 * kRedBlocks * t;
+  double* bb = part + (size_t)3 * kRedBlocks * t;
+  const unsigned eg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), kRedBlocks));
+
+  // R = B, U = 0, Z = P^{-1} R, D = Z
+  GP_TRY(copy_vectors(ctx, a.B, a.ldb, R, ld, n, t, 1.f));
+  GP_TRY(copy_vectors(ctx, nullptr, 0, a.U, a.ldu, n, t, 0.f));
+  GP_TRY(dot_columns(ctx, R, R, ld, n, t, bb));
+  GP_CUDA(ctx, cudaMemsetAsync(dflags, 0, 2 * sizeof(int), ctx->stream));
+  GP_TRY(precond_apply_impl(ctx, a.pc, n, R, Z, ld, t, nullptr, p_rz));
+  cg_init_kernel<<<1, 256, 0, ctx->stream>>>(sc, bb, p_rz, kRedBlocks, t, a.rz0,
+                                             a.iters_dev, a.relres_dev, dflags);
+  GP_LAUNCHED(ctx);
+  GP_TRY(copy_vectors(ctx, Z, ld, D, ld, n, t, 1.f));
+  if (a.Z0) GP_TRY(copy_vectors(ctx, Z, ld, a.Z0, ld, n, t, 1.f));
+  GP_CUDA(ctx, cudaMemsetAsync(a.alpha_hist, 0, sizeof(double) * (size_t)a.max_iter * t, ctx->stream));
+  GP_CUDA(ctx, cudaMemsetAsync(a.beta_hist, 0, sizeof(double) * (size_t)a.max_iter * t, ctx->stream));
+  GP_CUDA(ctx, cudaMemcpyAsync(flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  res->iters_max = 0;
+  res->n_kmv = 0;
+  res->breakdown = false;
+  res->converged = flags[0] == 0;
+  for (int it = 0; it < a.max_iter && flags[0] > 0; ++it) {
+    GP_TRY(kmv(ctx, p, p, D, ld, t, W, ld, a.s, a.sigma2, true, a.precision));
+    res->n_kmv++;
+    dot_partial_kernel<<<dim3(kRedBlocks, t), 256, 0, ctx->stream>>>(D, W, ld, n, sc, p_dw);
+    GP_LAUNCHED(ctx);
+    cg_alpha_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_dw, kRedBlocks, t, it, a.alpha_hist, dflags);
+    GP_LAUNCHED(ctx);
+    cg_update_kernel<<<dim3(kRedBlocks, t), 256, 0, ctx->stream>>>(a.U, R, D, W, ld, a.ldu, n, sc, p_rr);
+    GP_LAUNCHED(ctx);
+    GP_TRY(precond_apply_impl(ctx, a.pc, n, R, Z, ld, t, sc, p_rz));
+    cg_check_beta_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_rr, p_rz, kRedBlocks, t, it, a.tol,
+                                                     a.beta_hist, a.iters_dev, a.relres_dev, dflags);
+    GP_LAUNCHED(ctx);
+    cg_dupdate_kernel<<<dim3(eg, t), 256, 0, ctx->stream>>>(D, Z, ld, n, sc);
+    GP_LAUNCHED(ctx);
+    GP_CUDA(ctx, cudaMemcpyAsync(flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    res->iters_max = it + 1;
+    if (flags[1]) {
+      res->breakdown = true;
+      break;
+    }
+  }
+  res->converged = flags[0] == 0 && !res->breakdown;
+  return GP_OK;
+}
+
+}  // namespace gp

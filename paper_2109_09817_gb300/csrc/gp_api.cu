@@ -1,0 +1,677 @@
+// C ABI of libgp (declared in include/gp.h): contexts, workspace, and the
+// drivers of the exact-GP path of arXiv 2109.09817.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+#include "gp_internal.cuh"
+
+struct gp_model {
+  int device = 0;
+  int64_t n = 0, n_pad = 0;
+  int d = 0, d_pad = 0;
+  int precision = GP_FP32_PLAIN;
+  std::vector<double> ell;
+  double s = 1.0, sigma2 = 1e-4, tol = 1e-6;
+  int max_iter = 1000;
+  double* mu = nullptr;
+  float* xt = nullptr;
+  float* norm = nullptr;
+  float* xt_hi = nullptr;
+  float* xt_lo = nullptr;
+  __nv_bfloat16* xb_hi = nullptr;
+  __nv_bfloat16* xb_lo = nullptr;
+  float* alpha = nullptr;      // n_pad, zero padded
+  double* L = nullptr;         // n x k
+  int k = 0;
+  float* L32 = nullptr;
+  double* cfac = nullptr;
+  double pc_logdet = 0.0;
+};
+
+namespace gp {
+
+int set_err(gp_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int check_cuda(gp_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_err(ctx, GP_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return set_err(ctx, GP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* ws_get(gp_ctx* ctx, int slot, size_t bytes) {
+  DevBuf& b = ctx->ws[slot];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return b.p;
+  if (b.p) {
+    // kernels queued earlier may still read the old buffer
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  const size_t want = (bytes + 255) / 256 * 256;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return nullptr;
+  }
+  b.bytes = want;
+  return b.p;
+}
+
+void* pinned_get(gp_ctx* ctx, size_t bytes) {
+  if (ctx->pinned_bytes >= bytes) return ctx->pinned;
+  if (ctx->pinned) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_bytes = 0;
+  }
+  const size_t want = std::max<size_t>(bytes, 4096);
+  if (cudaMallocHost(&ctx->pinned, want) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->pinned = nullptr;
+    return nullptr;
+  }
+  ctx->pinned_bytes = want;
+  return ctx->pinned;
+}
+
+namespace {
+
+__global__ void var_from_dots_kernel(const double* __restrict__ dots, int64_t m,
+                                     double s, float* __restrict__ var) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    var[i] = (float)(s - dots[i]);
+}
+
+// out[i * ldo + a] = s * k(x_a, x'_i) for a < n (cross covariance columns),
+// from prepared features (same scaling and centring on both sides).
+__global__ void kcols_kernel(const float* __restrict__ xr, const float* __restrict__ nr,
+                             int64_t n, const float* __restrict__ xq,
+                             const float* __restrict__ nq, int64_t m, int d_pad,
+                             float s, float* __restrict__ out, int64_t ldo) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (a >= n || i >= m) return;
+  float dot = 0.f;
+  const float* xa = xr + a * d_pad;
+  const float* xi = xq + i * d_pad;
+  for (int j = 0; j < d_pad; ++j) dot = fmaf(xa[j], xi[j], dot);
+  const float u2 = fmaxf(nr[a] + nq[i] - 2.f * dot, 0.f);
+  float u, e;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(u) : "f"(u2));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-u));
+  out[i * ldo + a] = s * fmaf(u2, kC2, fmaf(u, kC1, 1.f)) * e;
+}
+
+int check_common(gp_ctx* ctx, const float* X, int64_t N, int d,
+                 const gp_theta* theta) {
+  if (!ctx) return GP_EINVAL;
+  if (!X || N <= 0 || d <= 0 || !theta || !theta->lengthscale)
+    return set_err(ctx, GP_EINVAL, "null pointer or non-positive size (N=%lld, d=%d)", (long long)N, d);
+  if (d > 256) return set_err(ctx, GP_EINVAL, "d = %d > 256", d);
+  if (!(theta->outputscale > 0.0) || !(theta->sigma2 > 0.0))
+    return set_err(ctx, GP_EINVAL, "outputscale and sigma2 must be > 0");
+  for (int j = 0; j < d; ++j)
+    if (!(theta->lengthscale[j] > 0.0) || !std::isfinite(theta->lengthscale[j]))
+      return set_err(ctx, GP_EINVAL, "lengthscale[%d] must be finite and > 0", j);
+  GP_CUDA(ctx, cudaSetDevice(ctx->device));
+  return GP_OK;
+}
+
+int prep_train(gp_ctx* ctx, const float* X, int64_t N, int d,
+               const gp_theta* theta, int precision, Prep* p) {
+  double* mu = ws<double>(ctx, WS_MU, (size_t)d);
+  if (!mu) return set_err(ctx, GP_ENOMEM, "workspace (mean)");
+  GP_TRY(feature_mean(ctx, X, N, d, mu));
+  return prepare_features(ctx, X, N, d, mu, theta->lengthscale, precision, WS_XT, p);
+}
+
+bool valid_precision(int p) { return p >= GP_FP32_PLAIN && p <= GP_BF16; }
+
+}  // namespace
+}  // namespace gp
+
+using namespace gp;
+
+extern "C" {
+
+int gp_create(gp_ctx** out, int device, void* stream) {
+  if (!out) return GP_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return GP_ECUDA;
+  }
+  gp_ctx* ctx = new gp_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+    ctx->num_sms = sms;
+  *out = ctx;
+  return GP_OK;
+}
+
+void gp_destroy(gp_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& e : ctx->ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto& b : ctx->ws)
+    if (b.p) cudaFree(b.p);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+int gp_set_stream(gp_ctx* ctx, void* stream) {
+  if (!ctx) return GP_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return GP_OK;
+}
+
+int gp_sync(gp_ctx* ctx) {
+  if (!ctx) return GP_EINVAL;
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return GP_OK;
+}
+
+const char* gp_last_error(const gp_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+int64_t gp_launch_count(const gp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int gp_profile(gp_ctx* ctx, int enable) {
+  if (!ctx) return GP_EINVAL;
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->prof = enable != 0;
+  ctx->ev_used = 0;
+  ctx->prof_flops = 0.0;
+  ctx->prof_elems = 0.0;
+  return GP_OK;
+}
+
+int gp_profile_read(gp_ctx* ctx, int64_t* products, double* ms, double* flops,
+                    double* entries) {
+  if (!ctx) return GP_EINVAL;
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double tot = 0.0;
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float e = 0.f;
+    GP_CUDA(ctx, cudaEventElapsedTime(&e, ctx->ev[i].first, ctx->ev[i].second));
+    tot += e;
+  }
+  if (products) *products = (int64_t)ctx->ev_used;
+  if (ms) *ms = tot;
+  if (flops) *flops = ctx->prof_flops;
+  if (entries) *entries = ctx->prof_elems;
+  return GP_OK;
+}
+
+int gp_kmatmul(gp_ctx* ctx, const float* X, int64_t N, int d,
+               const gp_theta* theta, const float* V, int t, float* out,
+               int precision) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (!V || !out || t < 1 || t > kMaxT || !valid_precision(precision))
+    return set_err(ctx, GP_EINVAL, "gp_kmatmul: bad V/out/t/precision");
+  if (V == out) return set_err(ctx, GP_EINVAL, "gp_kmatmul: out aliases V");
+  Prep p;
+  GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
+  return kmv(ctx, p, p, V, N, t, out, N, theta->outputscale, theta->sigma2, true, precision);
+}
+
+int gp_kcross_matmul(gp_ctx* ctx, const float* Xp, int64_t M, const float* X,
+                     int64_t N, int d, const gp_theta* theta, const float* V,
+                     int t, float* out, int precision) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (!Xp || M <= 0 || !V || !out || t < 1 || t > kMaxT || !valid_precision(precision))
+    return set_err(ctx, GP_EINVAL, "gp_kcross_matmul: bad arguments");
+  Prep p, q;
+  GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
+  GP_TRY(prepare_features(ctx, Xp, M, d, ws<double>(ctx, WS_MU, d), theta->lengthscale,
+                          precision, WS_XT2, &q));
+  return kmv(ctx, q, p, V, N, t, out, M, theta->outputscale, 0.0, false, precision);
+}
+
+int gp_pivchol(gp_ctx* ctx, const float* X, int64_t N, int d,
+               const gp_theta* theta, int k, double* L, int64_t* piv,
+               int* rank_out) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (k < 0 || k > N || (k > 0 && (!L || !piv)) || !rank_out)
+    return set_err(ctx, GP_EINVAL, "gp_pivchol: bad k/L/piv/rank_out");
+  *rank_out = 0;
+  if (k == 0) return GP_OK;
+  return pivchol_run(ctx, X, N, d, theta->lengthscale, theta->outputscale, k, L, piv, rank_out);
+}
+
+int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
+            const gp_theta* theta, const double* L, int k, const float* B,
+            int t, double tol, int max_iter, int precision, float* Omega,
+            double* alpha_hist, double* beta_hist, int* iters,
+            double* rel_resid) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (!B || !Omega || t < 1 || t > kMaxT || max_iter < 1 || !(tol >= 0.0) ||
+      k < 0 || (k > 0 && !L) || !valid_precision(precision))
+    return set_err(ctx, GP_EINVAL, "gp_mbcg: bad arguments");
+  Prep p;
+  GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
+  Precond pc;
+  GP_TRY(precond_setup(ctx, L, N, k, k, theta->sigma2, &pc));
+  double* ah = alpha_hist ? alpha_hist : ws<double>(ctx, WS_CG_AH, (size_t)max_iter * t);
+  double* bh = beta_hist ? beta_hist : ws<double>(ctx, WS_CG_BH, (size_t)max_iter * t);
+  int* iters_dev = static_cast<int*>(ws_get(ctx, WS_GR_ACC, sizeof(int) * t + sizeof(double) * t + 64));
+  if (!ah || !bh || !iters_dev) return set_err(ctx, GP_ENOMEM, "workspace (mbcg records)");
+  double* rr_dev = reinterpret_cast<double*>(iters_dev + ((t + 1) & ~1));
+  CgArgs a;
+  a.prep = &p;
+  a.s = theta->outputscale;
+  a.sigma2 = theta->sigma2;
+  a.pc = &pc;
+  a.B = B;
+  a.ldb = N;
+  a.t = t;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.precision = precision;
+  a.U = Omega;
+  a.ldu = N;
+  a.alpha_hist = ah;
+  a.beta_hist = bh;
+  a.iters_dev = iters_dev;
+  a.relres_dev = rr_dev;
+  CgResult res;
+  GP_TRY(mbcg_run(ctx, a, &res));
+  if (iters || rel_resid) {
+    char* h = static_cast<char*>(pinned_get(ctx, (sizeof(int) + sizeof(double)) * t + 64));
+    if (!h) return set_err(ctx, GP_ENOMEM, "pinned staging");
+    GP_CUDA(ctx, cudaMemcpyAsync(h, iters_dev, sizeof(int) * t, cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaMemcpyAsync(h + sizeof(int) * ((t + 1) & ~1), rr_dev, sizeof(double) * t,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (iters) std::memcpy(iters, h, sizeof(int) * t);
+    if (rel_resid) std::memcpy(rel_resid, h + sizeof(int) * ((t + 1) & ~1), sizeof(double) * t);
+  }
+  if (res.breakdown) return set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown (loss of definiteness)");
+  if (!res.converged) return set_err(ctx, GP_ENOTCONV, "mBCG: max_iter=%d reached", max_iter);
+  return GP_OK;
+}
+
+int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
+                      const gp_theta* theta, const float* y, int n_probes,
+                      uint64_t seed, int k, double tol, int max_iter,
+                      int precision, double* logml, double* logdet,
+                      double* grad, double* logdet_stderr, gp_stats* stats) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (!y || n_probes < 1 || n_probes > 255 || k < 0 || k > N || max_iter < 1 ||
+      !(tol >= 0.0) || !logml || !logdet || !valid_precision(precision))
+    return set_err(ctx, GP_EINVAL, "gp_logml_and_grad: bad arguments");
+  const double s = theta->outputscale, sig2 = theta->sigma2;
+  Prep p;
+  GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
+  const int64_t ld = p.n_pad;
+  const int T1 = 1 + n_probes;
+  // 1. preconditioner
+  double* L = ws<double>(ctx, WS_PC_L, (size_t)N * std::max(k, 1));
+  int64_t* piv = static_cast<int64_t*>(ws_get(ctx, WS_PC_PIV, sizeof(int64_t) * std::max(k, 1)));
+  if (!L || !piv) return set_err(ctx, GP_ENOMEM, "workspace (factor)");
+  int rank = 0;
+  if (k > 0) GP_TRY(pivchol_run(ctx, X, N, d, theta->lengthscale, s, k, L, piv, &rank));
+  Precond pc;
+  GP_TRY(precond_setup(ctx, L, N, k, rank, sig2, &pc));
+  // 2. right-hand sides [y | z_1..z_t]
+  float* B = ws<float>(ctx, WS_CG_B, (size_t)ld * T1);
+  float* U = ws<float>(ctx, WS_CG_U, (size_t)ld * T1);
+  float* Z0 = ws<float>(ctx, WS_CG_Z0, (size_t)ld * T1);
+  double* ah = ws<double>(ctx, WS_CG_AH, (size_t)max_iter * T1);
+  double* bh = ws<double>(ctx, WS_CG_BH, (size_t)max_iter * T1);
+  char* rec = static_cast<char*>(ws_get(ctx, WS_GR_ACC, 64 * 1024));
+  if (!B || !U || !Z0 || !ah || !bh || !rec) return set_err(ctx, GP_ENOMEM, "workspace (rhs)");
+  double* rz0 = reinterpret_cast<double*>(rec);            // T1
+  double* relres = rz0 + 256;                              // T1
+  double* quad = relres + 256;                             // T1
+  double* Gacc = quad + 256;                               // d_pad + 1
+  double* dots = Gacc + 512;                               // T1 + 1
+  int* iters = reinterpret_cast<int*>(dots + 512);         // T1
+  int* bad = iters + 256;
+  GP_CUDA(ctx, cudaMemsetAsync(B, 0, sizeof(float) * ld * T1, ctx->stream));
+  GP_CUDA(ctx, cudaMemsetAsync(U, 0, sizeof(float) * ld * T1, ctx->stream));
+  GP_CUDA(ctx, cudaMemsetAsync(Z0, 0, sizeof(float) * ld * T1, ctx->stream));
+  GP_CUDA(ctx, cudaMemsetAsync(rec, 0, 64 * 1024, ctx->stream));
+  GP_TRY(copy_vectors(ctx, y, N, B, ld, N, 1, 1.f));
+  GP_TRY(probe_vectors(ctx, L, N, rank, std::sqrt(sig2), seed, n_probes, B + ld, ld));
+  // 3. mBCG
+  CgArgs a;
+  a.prep = &p;
+  a.s = s;
+  a.sigma2 = sig2;
+  a.pc = &pc;
+  a.B = B;
+  a.ldb = ld;
+  a.t = T1;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.precision = precision;
+  a.U = U;
+  a.ldu = ld;
+  a.alpha_hist = ah;
+  a.beta_hist = bh;
+  a.Z0 = Z0;
+  a.rz0 = rz0;
+  a.iters_dev = iters;
+  a.relres_dev = relres;
+  CgResult res;
+  GP_TRY(mbcg_run(ctx, a, &res));
+  if (res.breakdown) return set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown (loss of definiteness)");
+  // 4. Lanczos quadrature over the probe columns
+  GP_TRY(lanczos_quadrature(ctx, ah, bh, T1, 1, n_probes, iters, max_iter, quad, bad));
+  // 5. y^T a
+  GP_TRY(dot_columns(ctx, B, U, ld, N, 1, dots));
+  // 6. gradient
+  float* Wg = nullptr;
+  if (grad) {
+    Wg = ws<float>(ctx, WS_GR_W, (size_t)ld * T1);
+    if (!Wg) return set_err(ctx, GP_ENOMEM, "workspace (grad)");
+    GP_CUDA(ctx, cudaMemsetAsync(Wg, 0, sizeof(float) * ld * T1, ctx->stream));
+    GP_TRY(copy_vectors(ctx, U, ld, Wg, ld, N, 1, 0.5f));
+    GP_TRY(copy_vectors(ctx, Z0 + ld, ld, Wg + ld, ld, N, n_probes, (float)(-0.5 / n_probes)));
+    GP_TRY(grad_tiles(ctx, p, U, Wg, T1, Gacc, nullptr));
+    GP_TRY(dot_columns(ctx, U, Wg, ld, N, T1, dots + 1));
+  }
+  // 7. host assembly
+  const size_t nrec = 64 * 1024;
+  char* h = static_cast<char*>(pinned_get(ctx, nrec));
+  if (!h) return set_err(ctx, GP_ENOMEM, "pinned staging");
+  GP_CUDA(ctx, cudaMemcpyAsync(h, rec, nrec, cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const double* h_rz0 = reinterpret_cast<const double*>(h);
+  const double* h_relres = h_rz0 + 256;
+  const double* h_quad = h_relres + 256;
+  const double* h_G = h_quad + 256;
+  const double* h_dots = h_G + 512;
+  const int* h_iters = reinterpret_cast<const int*>(h_dots + 512);
+  const int h_bad = h_iters[256];
+  if (h_bad) return set_err(ctx, GP_EBREAKDOWN, "Lanczos tridiagonal not positive definite (%d)", h_bad);
+  double acc = 0.0, acc2 = 0.0;
+  for (int c = 1; c <= n_probes; ++c) {
+    const double v = h_rz0[c] * h_quad[c - 1];
+    acc += v;
+    acc2 += v * v;
+  }
+  const double mean = acc / n_probes;
+  const double var = n_probes > 1 ? (acc2 - n_probes * mean * mean) / (n_probes - 1) : 0.0;
+  *logdet = pc.logdet + mean;
+  if (logdet_stderr) *logdet_stderr = std::sqrt(std::max(var, 0.0) / n_probes);
+  const double yKy = h_dots[0];
+  *logml = -0.5 * yKy - 0.5 * (*logdet) - 0.5 * (double)N * std::log(2.0 * M_PI);
+  if (grad) {
+    const double c2 = kFeatScale * kFeatScale;
+    for (int j = 0; j < d; ++j) grad[j] = 2.0 * s / (c2 * theta->lengthscale[j]) * h_G[j];
+    grad[d] = h_G[p.d_pad];
+    double gsig = 0.0;
+    for (int q = 0; q < T1; ++q) gsig += h_dots[1 + q];
+    grad[d + 1] = gsig;
+  }
+  if (stats) {
+    int im = 0;
+    double rm = 0.0;
+    for (int c = 0; c < T1; ++c) {
+      im = std::max(im, h_iters[c]);
+      rm = std::max(rm, h_relres[c]);
+    }
+    stats->iters_max = im;
+    stats->iters_y = h_iters[0];
+    stats->rank = rank;
+    stats->n_kmatmul = res.n_kmv;
+    stats->relres_y = h_relres[0];
+    stats->relres_max = rm;
+    stats->logdet_P = pc.logdet;
+    stats->yKinvy = yKy;
+  }
+  if (!res.converged) return set_err(ctx, GP_ENOTCONV, "mBCG: max_iter=%d reached", max_iter);
+  return GP_OK;
+}
+
+int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
+                 const gp_theta* theta, const float* y, int k, double tol,
+                 int max_iter, int precision, gp_model** out, gp_stats* stats) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (!y || !out || k < 0 || k > N || max_iter < 1 || !valid_precision(precision))
+    return set_err(ctx, GP_EINVAL, "gp_model_fit: bad arguments");
+  *out = nullptr;
+  Prep p;
+  GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
+  gp_model* m = new gp_model();
+  auto fail = [&](int rc) {
+    gp_model_free(m);
+    return rc;
+  };
+  m->device = ctx->device;
+  m->n = N;
+  m->n_pad = p.n_pad;
+  m->d = d;
+  m->d_pad = p.d_pad;
+  m->precision = precision;
+  m->ell.assign(theta->lengthscale, theta->lengthscale + d);
+  m->s = theta->outputscale;
+  m->sigma2 = theta->sigma2;
+  m->tol = tol;
+  m->max_iter = max_iter;
+  const size_t ne = (size_t)p.n_pad * p.d_pad;
+  if (cudaMalloc(&m->mu, sizeof(double) * d) != cudaSuccess ||
+      cudaMalloc(&m->xt, sizeof(float) * ne) != cudaSuccess ||
+      cudaMalloc(&m->norm, sizeof(float) * p.n_pad) != cudaSuccess ||
+      cudaMalloc(&m->alpha, sizeof(float) * p.n_pad) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
+  }
+  cudaStream_t st = ctx->stream;
+  GP_CUDA(ctx, cudaMemcpyAsync(m->mu, ws<double>(ctx, WS_MU, d), sizeof(double) * d, cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(ctx, cudaMemcpyAsync(m->xt, p.xt, sizeof(float) * ne, cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(ctx, cudaMemcpyAsync(m->norm, p.norm, sizeof(float) * p.n_pad, cudaMemcpyDeviceToDevice, st));
+  if (p.xt_hi) {
+    if (cudaMalloc(&m->xt_hi, sizeof(float) * ne) != cudaSuccess ||
+        cudaMalloc(&m->xt_lo, sizeof(float) * ne) != cudaSuccess)
+      return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->xt_hi, p.xt_hi, sizeof(float) * ne, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->xt_lo, p.xt_lo, sizeof(float) * ne, cudaMemcpyDeviceToDevice, st));
+  }
+  if (p.xb_hi) {
+    if (cudaMalloc(&m->xb_hi, 2 * ne) != cudaSuccess || cudaMalloc(&m->xb_lo, 2 * ne) != cudaSuccess)
+      return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->xb_hi, p.xb_hi, 2 * ne, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->xb_lo, p.xb_lo, 2 * ne, cudaMemcpyDeviceToDevice, st));
+  }
+  Prep mp = p;
+  mp.xt = m->xt;
+  mp.norm = m->norm;
+  mp.xt_hi = m->xt_hi;
+  mp.xt_lo = m->xt_lo;
+  mp.xb_hi = m->xb_hi;
+  mp.xb_lo = m->xb_lo;
+  // preconditioner
+  int rank = 0;
+  if (k > 0) {
+    if (cudaMalloc(&m->L, sizeof(double) * (size_t)N * k) != cudaSuccess)
+      return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
+    int64_t* piv = static_cast<int64_t*>(ws_get(ctx, WS_PC_PIV, sizeof(int64_t) * k));
+    if (!piv) return fail(set_err(ctx, GP_ENOMEM, "workspace"));
+    int rc = pivchol_run(ctx, X, N, d, theta->lengthscale, m->s, k, m->L, piv, &rank);
+    if (rc != GP_OK) return fail(rc);
+  }
+  Precond pc;
+  {
+    int rc = precond_setup(ctx, m->L, N, k, rank, m->sigma2, &pc);
+    if (rc != GP_OK) return fail(rc);
+  }
+  m->k = rank;
+  m->pc_logdet = pc.logdet;
+  if (rank > 0) {
+    if (cudaMalloc(&m->L32, sizeof(float) * (size_t)rank * pc.ld32) != cudaSuccess ||
+        cudaMalloc(&m->cfac, sizeof(double) * (size_t)2 * rank * rank) != cudaSuccess)
+      return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->L32, pc.L32, sizeof(float) * (size_t)rank * pc.ld32, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->cfac, pc.cfac, sizeof(double) * (size_t)rank * rank, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->cfac + (size_t)rank * rank, pc.cinv, sizeof(double) * (size_t)rank * rank,
+                                 cudaMemcpyDeviceToDevice, st));
+  }
+  // a = K-hat^{-1} y
+  GP_CUDA(ctx, cudaMemsetAsync(m->alpha, 0, sizeof(float) * p.n_pad, st));
+  double* ah = ws<double>(ctx, WS_CG_AH, (size_t)max_iter);
+  double* bh = ws<double>(ctx, WS_CG_BH, (size_t)max_iter);
+  int* rec = static_cast<int*>(ws_get(ctx, WS_GR_ACC, 256));
+  if (!ah || !bh || !rec) return fail(set_err(ctx, GP_ENOMEM, "workspace"));
+  CgArgs a;
+  a.prep = &mp;
+  a.s = m->s;
+  a.sigma2 = m->sigma2;
+  a.pc = &pc;
+  a.B = y;
+  a.ldb = N;
+  a.t = 1;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.precision = precision;
+  a.U = m->alpha;
+  a.ldu = p.n_pad;
+  a.alpha_hist = ah;
+  a.beta_hist = bh;
+  a.iters_dev = rec;
+  a.relres_dev = reinterpret_cast<double*>(rec + 2);
+  CgResult res;
+  {
+    int rc = mbcg_run(ctx, a, &res);
+    if (rc != GP_OK) return fail(rc);
+  }
+  if (stats) {
+    int* h = static_cast<int*>(pinned_get(ctx, 64));
+    GP_CUDA(ctx, cudaMemcpyAsync(h, rec, 16, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(ctx, cudaStreamSynchronize(st));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iters_max = stats->iters_y = h[0];
+    double rr;
+    std::memcpy(&rr, h + 2, sizeof(double));
+    stats->relres_y = stats->relres_max = rr;
+    stats->rank = rank;
+    stats->n_kmatmul = res.n_kmv;
+    stats->logdet_P = pc.logdet;
+  }
+  GP_CUDA(ctx, cudaStreamSynchronize(st));
+  if (res.breakdown) return fail(set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown"));
+  if (!res.converged) return fail(set_err(ctx, GP_ENOTCONV, "mBCG: max_iter=%d reached", max_iter));
+  *out = m;
+  return GP_OK;
+}
+
+void gp_model_free(gp_model* m) {
+  if (!m) return;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  for (void* q : {(void*)m->mu, (void*)m->xt, (void*)m->norm, (void*)m->xt_hi,
+                  (void*)m->xt_lo, (void*)m->xb_hi, (void*)m->xb_lo, (void*)m->alpha,
+                  (void*)m->L, (void*)m->L32, (void*)m->cfac})
+    if (q) cudaFree(q);
+  delete m;
+}
+
+int gp_predict(gp_ctx* ctx, const gp_model* m, const float* Xp, int64_t M,
+               float* mean, float* var, int var_mode) {
+  if (!ctx || !m || !Xp || M <= 0 || !mean) return set_err(ctx, GP_EINVAL, "gp_predict: bad arguments");
+  if (m->device != ctx->device) return set_err(ctx, GP_EINVAL, "gp_predict: model on another device");
+  GP_CUDA(ctx, cudaSetDevice(ctx->device));
+  Prep mp;
+  mp.n = m->n;
+  mp.n_pad = m->n_pad;
+  mp.d = m->d;
+  mp.d_pad = m->d_pad;
+  mp.xt = m->xt;
+  mp.norm = m->norm;
+  mp.xt_hi = m->xt_hi;
+  mp.xt_lo = m->xt_lo;
+  mp.xb_hi = m->xb_hi;
+  mp.xb_lo = m->xb_lo;
+  Prep q;
+  GP_TRY(prepare_features(ctx, Xp, M, m->d, m->mu, m->ell.data(), m->precision, WS_XT2, &q));
+  GP_TRY(kmv(ctx, q, mp, m->alpha, m->n_pad, 1, mean, M, m->s, 0.0, false, m->precision));
+  if (!var || var_mode == GP_VAR_NONE) return GP_OK;
+  if (var_mode != GP_VAR_EXACT) return set_err(ctx, GP_EINVAL, "gp_predict: unknown var_mode");
+  // exact latent variance: k(x',x') - k*^T K-hat^{-1} k*, in chunks of RHS
+  Precond pc;
+  pc.k = m->k;
+  pc.n = m->n;
+  pc.L = m->L;
+  pc.L32 = m->L32;
+  pc.ld32 = m->n_pad;
+  pc.cfac = m->cfac;
+  pc.cinv = m->cfac ? m->cfac + (size_t)m->k * m->k : nullptr;
+  pc.logdet = m->pc_logdet;
+  pc.sigma2 = m->sigma2;
+  const int CH = 64;
+  const int64_t ld = m->n_pad;
+  float* Kc = ws<float>(ctx, WS_PR_K, (size_t)ld * CH);
+  float* Om = ws<float>(ctx, WS_PR_O, (size_t)ld * CH);
+  double* ah = ws<double>(ctx, WS_CG_AH, (size_t)m->max_iter * CH);
+  double* bh = ws<double>(ctx, WS_CG_BH, (size_t)m->max_iter * CH);
+  char* rec = static_cast<char*>(ws_get(ctx, WS_GR_ACC, 8192));
+  if (!Kc || !Om || !ah || !bh || !rec) return set_err(ctx, GP_ENOMEM, "workspace (variance)");
+  int* itd = reinterpret_cast<int*>(rec);
+  double* rrd = reinterpret_cast<double*>(rec + 1024);
+  double* dots = reinterpret_cast<double*>(rec + 4096);
+  bool notconv = false;
+  for (int64_t i0 = 0; i0 < M; i0 += CH) {
+    const int nc = (int)std::min<int64_t>(CH, M - i0);
+    GP_CUDA(ctx, cudaMemsetAsync(Kc, 0, sizeof(float) * ld * nc, ctx->stream));
+    dim3 grid((unsigned)ceil_div(m->n, 256), (unsigned)nc);
+    kcols_kernel<<<grid, 256, 0, ctx->stream>>>(mp.xt, mp.norm, m->n, q.xt + i0 * q.d_pad,
+                                               q.norm + i0, nc, m->d_pad, (float)m->s, Kc, ld);
+    GP_LAUNCHED(ctx);
+    CgArgs a;
+    a.prep = &mp;
+    a.s = m->s;
+    a.sigma2 = m->sigma2;
+    a.pc = &pc;
+    a.B = Kc;
+    a.ldb = ld;
+    a.t = nc;
+    a.tol = m->tol;
+    a.max_iter = m->max_iter;
+    a.precision = m->precision;
+    a.U = Om;
+    a.ldu = ld;
+    a.alpha_hist = ah;
+    a.beta_hist = bh;
+    a.iters_dev = itd;
+    a.relres_dev = rrd;
+    CgResult res;
+    GP_TRY(mbcg_run(ctx, a, &res));
+    if (res.breakdown) return set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown (variance)");
+    notconv |= !res.converged;
+    GP_TRY(dot_columns(ctx, Kc, Om, ld, m->n, nc, dots));
+    var_from_dots_kernel<<<1, 256, 0, ctx->stream>>>(dots, nc, m->s, var + i0);
+    GP_LAUNCHED(ctx);
+  }
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (notconv) return set_err(ctx, GP_ENOTCONV, "variance solves reached max_iter");
+  return GP_OK;
+}
+
+}  // extern "C"

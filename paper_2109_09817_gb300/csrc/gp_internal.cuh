@@ -1,0 +1,217 @@
+// Internal declarations shared by the libgp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/gp.h"
+
+namespace gp {
+
+// ---------------------------------------------------------------------------
+// Feature scaling.  Prepared features are x~ = c (x - mu) / l with
+// c = sqrt(5) * log2(e), so that for two prepared rows
+//   u^2 = |x~_a|^2 + |x~_b|^2 - 2 x~_a . x~_b = (sqrt5 r log2 e)^2
+// and the Matern-5/2 kernel (Sec. 4) becomes
+//   k / s = (1 + ln2 u + (ln2)^2 u^2 / 3) 2^{-u},
+// one square root and one base-2 exponential per entry.
+// ---------------------------------------------------------------------------
+constexpr double kSqrt5 = 2.23606797749978969640917366873;
+constexpr double kLog2e = 1.44269504088896340735992468100;
+constexpr double kLn2 = 0.69314718055994530941723212146;
+constexpr double kFeatScale = kSqrt5 * kLog2e;
+constexpr float kC1 = 0.69314718055994530942f;   // ln 2
+constexpr float kC2 = 0.16014921423310860f;      // (ln 2)^2 / 3
+
+constexpr int kRowPad = 256;   // rows of prepared arrays are padded to this
+constexpr int kColPad = 32;    // features are padded to this (zeros)
+constexpr int kMaxT = 512;
+
+// Workspace slots owned by a context.  Each grows on demand.
+enum WsSlot {
+  WS_MU = 0, WS_SCALE, WS_PART,
+  WS_XT, WS_NORM, WS_XT_HI, WS_XT_LO, WS_XB_HI, WS_XB_LO,          // rows
+  WS_XT2, WS_NORM2, WS_XT2_HI, WS_XT2_LO, WS_XB2_HI, WS_XB2_LO,    // cross rows
+  WS_VHI, WS_VLO, WS_VBHI, WS_VBLO, WS_VPAD,
+  WS_CG_U, WS_CG_R, WS_CG_Z, WS_CG_D, WS_CG_W, WS_CG_Z0, WS_CG_B,
+  WS_CG_SCAL, WS_CG_PART, WS_CG_AH, WS_CG_BH, WS_CG_G,
+  WS_PC_L, WS_PC_L32, WS_PC_D, WS_PC_PIV, WS_PC_STATE, WS_PC_GRAM, WS_PC_CF,
+  WS_LZ_SCR, WS_LZ_OUT,
+  WS_GR_U, WS_GR_W, WS_GR_ACC,
+  WS_PR_K, WS_PR_O,
+  WS_COUNT
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace gp
+
+struct gp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 148;
+  std::string err;
+  int64_t launches = 0;
+  gp::DevBuf ws[gp::WS_COUNT];
+  void* pinned = nullptr;        // small pinned host staging area
+  size_t pinned_bytes = 0;
+  // K-hat V launch timing (gp_profile): one event pair per product
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t ev_used = 0;
+  double prof_flops = 0.0, prof_elems = 0.0;
+};
+
+namespace gp {
+
+// ---- error helpers --------------------------------------------------------
+int set_err(gp_ctx* ctx, int code, const char* fmt, ...);
+int check_cuda(gp_ctx* ctx, cudaError_t e, const char* what);
+#define GP_CUDA(ctx, call)                                        \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return ::gp::check_cuda(ctx, e_, #call); \
+  } while (0)
+#define GP_LAUNCHED(ctx)                                          \
+  do {                                                            \
+    (ctx)->launches++;                                            \
+    cudaError_t e_ = cudaGetLastError();                          \
+    if (e_ != cudaSuccess) return ::gp::check_cuda(ctx, e_, "kernel launch"); \
+  } while (0)
+#define GP_TRY(expr)                 \
+  do {                               \
+    int rc_ = (expr);                \
+    if (rc_ != GP_OK) return rc_;    \
+  } while (0)
+
+// Workspace: returns a device buffer of at least `bytes` for `slot`
+// (grown with cudaMalloc when needed; contents are not preserved).
+void* ws_get(gp_ctx* ctx, int slot, size_t bytes);
+template <class T>
+T* ws(gp_ctx* ctx, int slot, size_t count) {
+  return static_cast<T*>(ws_get(ctx, slot, count * sizeof(T)));
+}
+void* pinned_get(gp_ctx* ctx, size_t bytes);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---- prepared features ------------------------------------------------------
+struct Prep {
+  int64_t n = 0, n_pad = 0;
+  int d = 0, d_pad = 0;
+  const float* xt = nullptr;      // n_pad x d_pad, row-major, FP32
+  const float* norm = nullptr;    // n_pad
+  const float* xt_hi = nullptr;   // TF32-representable hi part (FP32 storage)
+  const float* xt_lo = nullptr;   // TF32 lo part
+  const __nv_bfloat16* xb_hi = nullptr;
+  const __nv_bfloat16* xb_lo = nullptr;
+};
+
+// mu (d doubles, device) = column means of X.
+int feature_mean(gp_ctx* ctx, const float* X, int64_t n, int d, double* mu);
+// Prepared features of X (n x d) with the given mu and l into the workspace
+// slots starting at `slot_xt` (WS_XT or WS_XT2).  `precision` decides which
+// split copies are built.
+int prepare_features(gp_ctx* ctx, const float* X, int64_t n, int d,
+                     const double* mu_dev, const double* lengthscale_host,
+                     int precision, int slot_xt, Prep* out);
+
+// ---- K-hat V ----------------------------------------------------------------
+// out(t vectors, ld ldo) = s K(rows, cols) V + (sym ? sigma2 V : 0).
+// V: t vectors of length cols.n with leading dimension ldv.
+// sym: rows and cols are the same point set (diagonal entries exact).
+int kmv(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V,
+        int64_t ldv, int t, float* out, int64_t ldo, double s, double sigma2,
+        bool sym, int precision);
+int kmv_plain(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V,
+              int64_t ldv, int t, float* out, int64_t ldo, float s, bool sym);
+int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V,
+           int64_t ldv, int t, float* out, int64_t ldo, float s, bool sym,
+           int precision);
+bool kmv_tc_supported(const Prep& rows, int t, int precision);
+// out = sigma2 * V (sym) or 0, rows of length n
+int kmv_init_out(gp_ctx* ctx, const float* V, int64_t ldv, int t, int64_t n,
+                 float* out, int64_t ldo, float sigma2);
+
+// ---- pivoted Cholesky (FP64) -------------------------------------------------
+struct Precond {
+  int k = 0;               // rank reached
+  int64_t n = 0;
+  const double* L = nullptr;     // n x k_alloc FP64 column-major (ld n)
+  const float* L32 = nullptr;    // FP32 copy, ld n_pad
+  int64_t ld32 = 0;
+  const double* cfac = nullptr;  // k x k lower Cholesky of sigma2 I + L^T L
+  const double* cinv = nullptr;  // (sigma2 I + L^T L)^{-1}, k x k, FP64
+  double logdet = 0.0;           // log|P|
+  double sigma2 = 0.0;
+};
+int pivchol_run(gp_ctx* ctx, const float* X, int64_t n, int d,
+                const double* lengthscale_host, double s, int k, double* L,
+                int64_t* piv, int* rank_out);
+int precond_setup(gp_ctx* ctx, const double* L, int64_t n, int k_alloc,
+                  int rank, double sigma2, Precond* out);
+
+// ---- mBCG --------------------------------------------------------------------
+struct CgResult {
+  int iters_max = 0;
+  int n_kmv = 0;
+  bool converged = false;
+  bool breakdown = false;
+};
+struct CgArgs {
+  const Prep* prep = nullptr;
+  double s = 1.0, sigma2 = 1e-4;
+  const Precond* pc = nullptr;   // null: P = sigma2 I
+  const float* B = nullptr;      // t vectors, ld ldb
+  int64_t ldb = 0;
+  int t = 0;
+  double tol = 1e-6;
+  int max_iter = 1000;
+  int precision = GP_FP32_PLAIN;
+  float* U = nullptr;            // solution, t vectors, ld ldu
+  int64_t ldu = 0;
+  double* alpha_hist = nullptr;  // max_iter*t (device, required)
+  double* beta_hist = nullptr;
+  float* Z0 = nullptr;           // optional: P^{-1} B out (ld n_pad)
+  double* rz0 = nullptr;         // optional device t: r0^T z0
+  int* iters_dev = nullptr;      // device t
+  double* relres_dev = nullptr;  // device t
+};
+int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res);
+// Z = P^{-1} R for t vectors (ld ld), optional rz[c] += R_c . Z_c partials
+int precond_apply(gp_ctx* ctx, const Precond* pc, int64_t n, const float* R,
+                  float* Z, int64_t ld, int t, const int* active,
+                  double* rz_out);
+
+// ---- Lanczos quadrature ---------------------------------------------------------
+// quad[c] = e1^T log(T_c) e1 for columns c0..c0+nc-1 of the histories.
+int lanczos_quadrature(gp_ctx* ctx, const double* alpha_hist,
+                       const double* beta_hist, int t, int c0, int nc,
+                       const int* iters_dev, int max_iter, double* quad_dev,
+                       int* bad_dev);
+
+// ---- gradient -----------------------------------------------------------------
+// G[j] (d_pad doubles) and gs (1 double) accumulated by the backward kernel
+// for M_sym = 1/2 (U W^T + W U^T), U, W: T1 vectors of length n (ld n_pad).
+int grad_tiles(gp_ctx* ctx, const Prep& p, const float* U, const float* W,
+               int T1, double* G, double* gs);
+
+// ---- small helpers (cg.cu) ------------------------------------------------------
+// out[c] = sum_a A[c*ld + a] * B[c*ld + a] in FP64, c < t (device doubles)
+int dot_columns(gp_ctx* ctx, const float* A, const float* B, int64_t ld,
+                int64_t n, int t, double* out);
+int probe_vectors(gp_ctx* ctx, const double* L, int64_t n, int k, double sigma,
+                  uint64_t seed, int n_probes, float* Z, int64_t ldz);
+int copy_vectors(gp_ctx* ctx, const float* src, int64_t lds, float* dst,
+                 int64_t ldd, int64_t n, int t, float scale);
+
+}  // namespace gp

@@ -1,0 +1,374 @@
+// Pivoted Cholesky preconditioner in FP64 (A7).
+//
+// arXiv 2109.09817 Sec. 3.2: BBMM preconditions CG with a pivoted Cholesky
+// factor (refs. bach2013sharp, harbrecht2012low).  Greedy rank-k factor
+// K ~ L L^T: at step j pick p = argmax of the residual diagonal
+// d = diag(K - L L^T) (lowest index on ties), form the kernel column
+// K(X, x_p) in FP64 by direct differences, subtract L_{:,<j} L_{p,<j}^T,
+// divide by sqrt(d_p), update d -= l_j^2 and take p out (d_p = 0).
+// Stops early when max d <= 1e-12 s.  P = L L^T + sigma^2 I is applied by
+// the Woodbury identity with the k x k factor of sigma^2 I + L^T L (FP64).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gp_internal.cuh"
+
+namespace gp {
+namespace {
+
+struct PcState {
+  double dtop;
+  int piv;
+  int rank;
+  int stop;
+  int bad;
+};
+
+constexpr int kArgBlocks = 512;
+
+__device__ __forceinline__ void better(double& v, int64_t& i, double v2, int64_t i2) {
+  // larger value wins; equal values: lower index wins; NaN loses
+  if (v2 > v || (v2 == v && i2 < i) || (v != v && v2 == v2)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+__global__ void pc_init_kernel(double* dres, int64_t n, double s, PcState* st) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x)
+    dres[a] = s;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->dtop = 0.0;
+    st->piv = -1;
+    st->rank = 0;
+    st->stop = 0;
+    st->bad = 0;
+  }
+}
+
+__global__ void pc_argmax_partial(const double* __restrict__ dres, int64_t n,
+                                  double* __restrict__ pv, int64_t* __restrict__ pi,
+                                  const PcState* st) {
+  if (st->stop) return;
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  double v = -1.0;
+  int64_t idx = INT64_MAX;
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x)
+    better(v, idx, dres[a], a);
+  sv[threadIdx.x] = v;
+  si[threadIdx.x] = idx;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      double v2 = sv[threadIdx.x + off];
+      int64_t i2 = si[threadIdx.x + off];
+      double v1 = sv[threadIdx.x];
+      int64_t i1 = si[threadIdx.x];
+      better(v1, i1, v2, i2);
+      sv[threadIdx.x] = v1;
+      si[threadIdx.x] = i1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = sv[0];
+    pi[blockIdx.x] = si[0];
+  }
+}
+
+__global__ void pc_argmax_final(const double* __restrict__ pv,
+                                const int64_t* __restrict__ pi, int nparts,
+                                double thresh, int j, int64_t* __restrict__ piv,
+                                PcState* st) {
+  if (st->stop) return;
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  double v = -1.0;
+  int64_t idx = INT64_MAX;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) better(v, idx, pv[b], pi[b]);
+  sv[threadIdx.x] = v;
+  si[threadIdx.x] = idx;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      double v1 = sv[threadIdx.x];
+      int64_t i1 = si[threadIdx.x];
+      better(v1, i1, sv[threadIdx.x + off], si[threadIdx.x + off]);
+      sv[threadIdx.x] = v1;
+      si[threadIdx.x] = i1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double top = sv[0];
+    if (!(top == top) || isinf(top)) {
+      st->bad = 1;
+      st->stop = 1;
+      return;
+    }
+    if (top <= thresh) {
+      st->stop = 1;
+      return;
+    }
+    st->dtop = top;
+    st->piv = (int)si[0];
+    piv[j] = si[0];
+    st->rank = j + 1;
+  }
+}
+
+// Column j of L and the residual-diagonal update; one thread per row.
+__global__ void pc_column_kernel(const float* __restrict__ X, int64_t n, int d,
+                                 const double* __restrict__ inv_l, double s,
+                                 double* __restrict__ L, double* __restrict__ dres,
+                                 int j, const PcState* __restrict__ st) {
+  extern __shared__ double shp[];   // d pivot features, then j pivot-row L entries
+  if (st->stop) return;
+  const int p = st->piv;
+  double* xp = shp;
+  double* lp = shp + d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) xp[i] = (double)X[(int64_t)p * d + i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) lp[i] = L[(int64_t)i * n + p];
+  __syncthreads();
+  const double inv_sq = 1.0 / sqrt(st->dtop);
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    double r2 = 0.0;
+    const float* xa = X + a * d;
+    for (int i = 0; i < d; ++i) {
+      const double u = ((double)xa[i] - xp[i]) * inv_l[i];
+      r2 += u * u;
+    }
+    const double r = sqrt(r2);
+    const double sr = kSqrt5 * r;
+    double col = s * (1.0 + sr + (5.0 / 3.0) * r2) * exp(-sr);
+    for (int i = 0; i < j; ++i) col -= L[(int64_t)i * n + a] * lp[i];
+    const double l = col * inv_sq;
+    L[(int64_t)j * n + a] = l;
+    dres[a] = (a == p) ? 0.0 : dres[a] - l * l;
+  }
+}
+
+__global__ void pc_rank_kernel(const PcState* st, int* rank, int* bad) {
+  *rank = st->rank;
+  *bad = st->bad;
+}
+
+// Gram matrix G = L^T L (rank x rank, FP64), partial sums over row chunks.
+// grid = (row chunks, pair chunks of 8*256); each thread owns up to 8 pairs
+// (i, jj), i >= jj, of the packed lower triangle.
+__device__ __forceinline__ void unrank_pair(int pidx, int& i, int& jj) {
+  i = (int)((sqrt(8.0 * pidx + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > pidx) --i;
+  while ((i + 1) * (i + 2) / 2 <= pidx) ++i;
+  jj = pidx - i * (i + 1) / 2;
+}
+
+__global__ void pc_gram_partial(const double* __restrict__ L, int64_t n, int k,
+                                int64_t rows_per_blk, double* __restrict__ part) {
+  extern __shared__ double sl[];   // 32 rows x k
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+  const int64_t r1 = min(n, r0 + rows_per_blk);
+  const int npairs = k * (k + 1) / 2;
+  const int pbase = blockIdx.y * 8 * blockDim.x;
+  double acc[8];
+  int pi_[8], pj_[8];
+  for (int q = 0; q < 8; ++q) {
+    acc[q] = 0.0;
+    const int pidx = pbase + threadIdx.x + q * blockDim.x;
+    pi_[q] = -1;
+    pj_[q] = 0;
+    if (pidx < npairs) unrank_pair(pidx, pi_[q], pj_[q]);
+  }
+  for (int64_t rb = r0; rb < r1; rb += 32) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * k; idx += blockDim.x) {
+      const int rr = idx % 32, c = idx / 32;
+      const int64_t row = rb + rr;
+      sl[rr * k + c] = row < r1 ? L[(int64_t)c * n + row] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (pi_[q] < 0) continue;
+      double a = acc[q];
+      for (int rr = 0; rr < 32; ++rr) a += sl[rr * k + pi_[q]] * sl[rr * k + pj_[q]];
+      acc[q] = a;
+    }
+  }
+  for (int q = 0; q < 8; ++q) {
+    const int pidx = pbase + threadIdx.x + q * blockDim.x;
+    if (pidx < npairs) part[(int64_t)blockIdx.x * npairs + pidx] = acc[q];
+  }
+}
+
+// C = sigma2 I + G; in-place lower Cholesky (one block); logdet of C.
+__global__ void pc_small_chol(const double* __restrict__ part, int nparts, int k,
+                              double sigma2, double* __restrict__ C,
+                              double* __restrict__ logdet_out, int* bad) {
+  const int npairs = k * (k + 1) / 2;
+  for (int pidx = threadIdx.x; pidx < npairs; pidx += blockDim.x) {
+    int i, jj;
+    unrank_pair(pidx, i, jj);
+    double g = 0.0;
+    for (int b = 0; b < nparts; ++b) g += part[(int64_t)b * npairs + pidx];
+    if (i == jj) g += sigma2;
+    C[i * k + jj] = g;
+    C[jj * k + i] = (i == jj) ? g : 0.0;   // upper part cleared below
+  }
+  __syncthreads();
+  // right-looking Cholesky on the lower triangle
+  for (int c = 0; c < k; ++c) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double dg = C[c * k + c];
+      if (!(dg > 0.0)) *bad = 1;
+      C[c * k + c] = sqrt(fmax(dg, 1e-300));
+    }
+    __syncthreads();
+    const double piv = C[c * k + c];
+    for (int r = c + 1 + threadIdx.x; r < k; r += blockDim.x) C[r * k + c] /= piv;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (k - c - 1) * (k - c - 1); idx += blockDim.x) {
+      const int r = c + 1 + idx / (k - c - 1);
+      const int q = c + 1 + idx % (k - c - 1);
+      if (q <= r) C[r * k + q] -= C[r * k + c] * C[q * k + c];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ld = 0.0;
+    for (int c = 0; c < k; ++c) ld += 2.0 * log(C[c * k + c]);
+    *logdet_out = ld;
+  }
+}
+
+// Cinv = (F F^T)^{-1} from the lower factor F (k x k): column q of the
+// inverse solves F F^T x = e_q; one thread per column.
+__global__ void pc_small_inverse(const double* __restrict__ F, int k,
+                                 double* __restrict__ Cinv) {
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    double* x = Cinv + (int64_t)q * k;   // column q (symmetric result)
+    for (int j = 0; j < k; ++j) {
+      double s = (j == q) ? 1.0 : 0.0;
+      for (int i = 0; i < j; ++i) s -= F[j * k + i] * x[i];
+      x[j] = s / F[j * k + j];
+    }
+    for (int j = k - 1; j >= 0; --j) {
+      double s = x[j];
+      for (int i = j + 1; i < k; ++i) s -= F[i * k + j] * x[i];
+      x[j] = s / F[j * k + j];
+    }
+  }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ L, int64_t n, int k,
+                              float* __restrict__ L32, int64_t ld32) {
+  const int64_t total = (int64_t)k * ld32;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / ld32, a = i % ld32;
+    L32[i] = a < n ? (float)L[c * n + a] : 0.f;
+  }
+}
+
+}  // namespace
+
+int pivchol_run(gp_ctx* ctx, const float* X, int64_t n, int d,
+                const double* lengthscale_host, double s, int k, double* L,
+                int64_t* piv, int* rank_out) {
+  double* dres = ws<double>(ctx, WS_PC_D, (size_t)n);
+  PcState* st = static_cast<PcState*>(ws_get(ctx, WS_PC_STATE, sizeof(PcState) + 64));
+  double* pv = ws<double>(ctx, WS_PC_GRAM, 2 * kArgBlocks);
+  double* inv_l = ws<double>(ctx, WS_SCALE, (size_t)d);
+  double* hst = static_cast<double*>(pinned_get(ctx, sizeof(double) * (size_t)(d + 2)));
+  if (!dres || !st || !pv || !inv_l || !hst) return set_err(ctx, GP_ENOMEM, "workspace (pivchol)");
+  int64_t* pi = reinterpret_cast<int64_t*>(pv + kArgBlocks);
+  for (int i = 0; i < d; ++i) hst[i] = 1.0 / lengthscale_host[i];
+  GP_CUDA(ctx, cudaMemcpyAsync(inv_l, hst, sizeof(double) * d, cudaMemcpyHostToDevice, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  GP_CUDA(ctx, cudaMemsetAsync(L, 0, sizeof(double) * (size_t)n * k, ctx->stream));
+  GP_CUDA(ctx, cudaMemsetAsync(piv, 0xff, sizeof(int64_t) * (size_t)k, ctx->stream));
+  const unsigned eg = (unsigned)std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms);
+  pc_init_kernel<<<std::max(1u, eg), 256, 0, ctx->stream>>>(dres, n, s, st);
+  GP_LAUNCHED(ctx);
+  const int nparts = (int)std::min<int64_t>(kArgBlocks, std::max<int64_t>(1, ceil_div(n, 2048)));
+  const double thresh = 1e-12 * s;
+  for (int j = 0; j < k; ++j) {
+    pc_argmax_partial<<<nparts, 256, 0, ctx->stream>>>(dres, n, pv, pi, st);
+    GP_LAUNCHED(ctx);
+    pc_argmax_final<<<1, 256, 0, ctx->stream>>>(pv, pi, nparts, thresh, j, piv, st);
+    GP_LAUNCHED(ctx);
+    const size_t shm = sizeof(double) * (size_t)(d + j + 1);
+    pc_column_kernel<<<std::max(1u, eg), 256, shm, ctx->stream>>>(X, n, d, inv_l, s, L, dres, j, st);
+    GP_LAUNCHED(ctx);
+  }
+  int* hr = static_cast<int*>(pinned_get(ctx, 2 * sizeof(int)));
+  int* dr = reinterpret_cast<int*>(reinterpret_cast<char*>(st) + sizeof(PcState));
+  pc_rank_kernel<<<1, 1, 0, ctx->stream>>>(st, dr, dr + 1);
+  GP_LAUNCHED(ctx);
+  GP_CUDA(ctx, cudaMemcpyAsync(hr, dr, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *rank_out = hr[0];
+  if (hr[1]) return set_err(ctx, GP_ENONPD, "pivoted Cholesky: non-finite residual diagonal at step %d", hr[0]);
+  return GP_OK;
+}
+
+int precond_setup(gp_ctx* ctx, const double* L, int64_t n, int k_alloc,
+                  int rank, double sigma2, Precond* out) {
+  Precond pc;
+  pc.n = n;
+  pc.k = rank;
+  pc.L = L;
+  pc.sigma2 = sigma2;
+  pc.ld32 = round_up(std::max<int64_t>(n, 1), kRowPad);
+  (void)k_alloc;
+  if (rank == 0) {
+    pc.logdet = (double)n * std::log(sigma2);
+    *out = pc;
+    return GP_OK;
+  }
+  float* L32 = ws<float>(ctx, WS_PC_L32, (size_t)rank * pc.ld32);
+  double* cf = ws<double>(ctx, WS_PC_CF, (size_t)2 * rank * rank + 8);
+  const int npairs = rank * (rank + 1) / 2;
+  const int nblk = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 4096)), 2 * ctx->num_sms);
+  const int64_t rows_per_blk = ceil_div(n, nblk);
+  double* part = ws<double>(ctx, WS_PC_GRAM, (size_t)nblk * npairs + 2 * kArgBlocks);
+  if (!L32 || !cf || !part) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner)");
+  const unsigned eg = (unsigned)std::min<int64_t>(ceil_div((int64_t)rank * pc.ld32, 256), 16LL * ctx->num_sms);
+  to_f32_kernel<<<eg, 256, 0, ctx->stream>>>(L, n, rank, L32, pc.ld32);
+  GP_LAUNCHED(ctx);
+  const size_t shm = sizeof(double) * 32 * rank;
+  if (shm > 48 * 1024) {
+    GP_CUDA(ctx, cudaFuncSetAttribute(pc_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  }
+  dim3 ggrid(nblk, (unsigned)ceil_div(npairs, 8 * 256));
+  pc_gram_partial<<<ggrid, 256, shm, ctx->stream>>>(L, n, rank, rows_per_blk, part);
+  GP_LAUNCHED(ctx);
+  double* cinv = cf + (size_t)rank * rank;
+  double* ld_dev = cinv + (size_t)rank * rank;
+  int* bad_dev = reinterpret_cast<int*>(ld_dev + 1);
+  GP_CUDA(ctx, cudaMemsetAsync(bad_dev, 0, sizeof(int), ctx->stream));
+  pc_small_chol<<<1, 256, 0, ctx->stream>>>(part, nblk, rank, sigma2, cf, ld_dev, bad_dev);
+  GP_LAUNCHED(ctx);
+  pc_small_inverse<<<1, 128, 0, ctx->stream>>>(cf, rank, cinv);
+  GP_LAUNCHED(ctx);
+  double* hb = static_cast<double*>(pinned_get(ctx, 2 * sizeof(double)));
+  GP_CUDA(ctx, cudaMemcpyAsync(hb, ld_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  int bad = 0;
+  std::memcpy(&bad, hb + 1, sizeof(int));
+  if (bad) return set_err(ctx, GP_ENONPD, "sigma^2 I + L^T L is not positive definite");
+  pc.logdet = (double)(n - rank) * std::log(sigma2) + hb[0];
+  pc.L32 = L32;
+  pc.cfac = cf;
+  pc.cinv = cinv;
+  *out = pc;
+  return GP_OK;
+}
+
+}  // namespace gp

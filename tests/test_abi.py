@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads without a GPU, and exports every symbol
+include/gp.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gp.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^GP_API\s+[\w\s\*]*?\b(gp_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2109_09817_gb300.build import build
+    try:
+        return build()
+    except RuntimeError as e:  # pragma: no cover
+        if "nvcc not found" in str(e):
+            pytest.skip("nvcc not available")
+        raise
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("gp_kmatmul", "gp_pivchol", "gp_mbcg", "gp_logml_and_grad",
+                     "gp_predict", "gp_model_fit", "gp_create", "gp_destroy"):
+        assert required in names
+    from paper_2109_09817_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s+(gp_\w+)", out))
+    assert set(_declared()) <= exported
+    # internal symbols stay hidden
+    assert all(n.startswith("gp_") for n in exported)
+
+
+def test_library_loads_without_gpu(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in _declared():
+        assert hasattr(lib, name)
+    from paper_2109_09817_gb300 import _lib
+    _lib.load(lib_path)
+
+
+def test_product_path_has_no_fallback(tmp_path, monkeypatch):
+    from paper_2109_09817_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="libgp.so not found"):
+        _lib.load(str(tmp_path / "missing.so"))

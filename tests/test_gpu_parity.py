@@ -1,0 +1,258 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative, max over columns of the 2-norm error unless stated):
+K-hat V 1e-5 (FP32 modes); solve true residual 1e-4; predictive mean 1e-4;
+log-det 1e-3 against the same-probe target; gradient 1e-3 of the largest
+component against the same-probe gradient; pivots identical where the
+oracle's residual-diagonal gap exceeds 1e-9 s.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import gp_oracle as go  # noqa: E402
+from synth import make_workload  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_09817_gb300 as gp_
+    return gp_
+
+
+@pytest.fixture(scope="module")
+def ctx(gp):
+    c = gp.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def w2k():
+    return make_workload("gp2k")
+
+
+def _relerr(got, ref):
+    got = np.asarray(got, np.float64).reshape(ref.shape)
+    num = np.linalg.norm(got - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    return float(np.max(num / np.maximum(den, 1e-300)))
+
+
+def _theta(gp, w):
+    return gp.Theta(w.lengthscale, w.outputscale, w.sigma2)
+
+
+# ---------------------------------------------------------------- K-hat V ----
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_kmatmul_gp2k(gp, ctx, w2k, precision):
+    w = w2k
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((16, w.N)).astype(np.float32)
+    out = gp.gp_kmatmul(ctx, torch.from_numpy(w.X).cuda(), _theta(gp, w),
+                        torch.from_numpy(V).cuda(), gp.PRECISIONS[precision])
+    ref = go.khat_matmul(w.X, V.T.astype(np.float64), w.lengthscale, 1.0, w.sigma2)
+    assert _relerr(out.cpu().numpy().T, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("N,d,t", [(1, 1, 1), (7, 3, 2), (129, 5, 3), (257, 33, 17),
+                                   (1000, 64, 65), (300, 8, 100), (130, 2, 1)])
+def test_kmatmul_ragged(gp, ctx, N, d, t):
+    rng = np.random.default_rng(N + d + t)
+    X = rng.standard_normal((N, d)).astype(np.float32)
+    ell = rng.uniform(0.5, 2.0, d)
+    V = rng.standard_normal((t, N)).astype(np.float32)
+    th = gp.Theta(ell, 0.7, 1e-3)
+    out = gp.gp_kmatmul(ctx, torch.from_numpy(X).cuda(), th, torch.from_numpy(V).cuda())
+    ref = go.khat_matmul(X, V.T.astype(np.float64), ell, 0.7, 1e-3)
+    assert _relerr(out.cpu().numpy().T, ref) <= 1e-5
+
+
+def test_kmatmul_single_point_is_exact(gp, ctx):
+    X = torch.tensor([[0.3, -1.2]], device="cuda")
+    V = torch.tensor([[2.0], [-0.5]], device="cuda")
+    out = gp.gp_kmatmul(ctx, X, gp.Theta(np.array([1.0, 2.0]), 1.5, 0.25), V)
+    assert torch.allclose(out.cpu(), torch.tensor([[3.5], [-0.875]]))
+
+
+def test_kcross_matmul(gp, ctx, w2k):
+    w = w2k
+    rng = np.random.default_rng(1)
+    V = rng.standard_normal((3, w.N)).astype(np.float32)
+    out = gp.gp_kcross_matmul(ctx, torch.from_numpy(w.Xtest).cuda(), torch.from_numpy(w.X).cuda(),
+                              _theta(gp, w), torch.from_numpy(V).cuda())
+    ref = go.kcross_matmul(w.Xtest, w.X, V.T.astype(np.float64), w.lengthscale, 1.0)
+    assert _relerr(out.cpu().numpy().T, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("name,t,nrows", [("gp64k", 32, 256), ("gp1m", 16, 48)])
+def test_kmatmul_full_size_sampled_rows(gp, ctx, name, t, nrows):
+    """At the full workload sizes: rows sampled and formed one by one by the
+    oracle (FP64, streamed); error measured over the sampled rows."""
+    w = make_workload(name)
+    rng = np.random.default_rng(7)
+    V = rng.choice([-1.0, 1.0], size=(t, w.N)).astype(np.float32)
+    out = gp.gp_kmatmul(ctx, torch.from_numpy(w.X).cuda(), _theta(gp, w),
+                        torch.from_numpy(V).cuda()).cpu().numpy().T
+    rows = np.sort(rng.choice(w.N, size=nrows, replace=False))
+    ref = go.khat_matmul_rows(w.X, V.T.astype(np.float64), w.lengthscale, 1.0, w.sigma2, rows)
+    assert _relerr(out[rows], ref) <= 1e-5
+
+
+# ------------------------------------------------------- pivoted Cholesky ----
+def test_pivchol_matches_oracle(gp, ctx, w2k):
+    w = w2k
+    k = 32
+    L, piv, rank = gp.gp_pivchol(ctx, torch.from_numpy(w.X).cuda(), _theta(gp, w), k)
+    Lr, pr, gaps = go.pivoted_cholesky(w.X, w.lengthscale, 1.0, k)
+    assert rank == len(pr) == k
+    piv = piv.cpu().numpy()
+    # identical sequences, except that a step whose top-two residual gap is
+    # <= 1e-9 s may legitimately differ (after which the sequences diverge)
+    for j in range(k):
+        if piv[j] != pr[j]:
+            assert gaps[j] <= 1e-9, (j, piv[j], pr[j], gaps[j])
+            break
+    else:
+        np.testing.assert_allclose(L.cpu().numpy().T, Lr, atol=1e-9)
+
+
+def test_pivchol_early_stop_on_duplicates(gp, ctx):
+    X = np.repeat(np.random.default_rng(2).standard_normal((3, 4)), 5, axis=0).astype(np.float32)
+    L, piv, rank = gp.gp_pivchol(ctx, torch.from_numpy(X).cuda(), gp.Theta(np.ones(4)), 8)
+    Lr, pr, _ = go.pivoted_cholesky(X, np.ones(4), 1.0, 8)
+    assert rank == len(pr) == 3
+    np.testing.assert_array_equal(piv.cpu().numpy()[:3], pr)
+    assert np.all(piv.cpu().numpy()[3:] == -1)
+
+
+# ------------------------------------------------------------------- mBCG ----
+def test_mbcg_solves_to_tolerance(gp, ctx, w2k):
+    w = w2k
+    X = torch.from_numpy(w.X).cuda()
+    th = _theta(gp, w)
+    L, piv, rank = gp.gp_pivchol(ctx, X, th, 32)
+    rng = np.random.default_rng(3)
+    B = np.vstack([w.y, rng.choice([-1.0, 1.0], size=(15, w.N))]).astype(np.float32)
+    r = gp.gp_mbcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=1e-6, max_iter=1000)
+    Om = r["Omega"].cpu().numpy().T.astype(np.float64)
+    res = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
+    assert res.max() <= 1e-4, res
+    Kh = go.khat_matrix(w.X, w.lengthscale, 1.0, w.sigma2)
+    ref = go.cholesky_solve(Kh, B.T.astype(np.float64))
+    assert _relerr(Om, ref) <= 1e-3
+    assert np.all(r["iters"] > 0)
+
+
+def test_mbcg_iterations_follow_the_oracle(gp, ctx):
+    """Near-duplicate rows (sigma^2 = 1e-4): the GPU's FP32 PCG takes about
+    as many steps as the oracle's FP64 PCG, and its y column meets 1e-4."""
+    w = make_workload("gp64k", N=4096)
+    X = torch.from_numpy(w.X).cuda()
+    th = _theta(gp, w)
+    L, piv, rank = gp.gp_pivchol(ctx, X, th, 64)
+    B = w.y[None, :].astype(np.float32)
+    r = gp.gp_mbcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=1e-4, max_iter=2000)
+    Lr, _, _ = go.pivoted_cholesky(w.X, w.lengthscale, 1.0, 64)
+    Kh = go.khat_matrix(w.X, w.lengthscale, 1.0, w.sigma2)
+    ref = go.mbcg(lambda V: Kh @ V, B.T.astype(np.float64),
+                  lambda R: go.precond_solve(Lr, w.sigma2, R), 1e-4, 2000)
+    assert r["rc"] == 0
+    assert abs(int(r["iters"][0]) - int(ref["iters"][0])) <= 0.25 * ref["iters"][0] + 5
+    Om = r["Omega"].cpu().numpy().T.astype(np.float64)
+    res = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
+    assert res.max() <= 2e-4
+
+
+def test_mbcg_unpreconditioned_and_zero_column(gp, ctx):
+    w = make_workload("gp2k", N=400, d=6)
+    X = torch.from_numpy(w.X).cuda()
+    B = np.vstack([w.y, np.zeros(w.N)]).astype(np.float32)
+    r = gp.gp_mbcg(ctx, X, _theta(gp, w), None, torch.from_numpy(B).cuda(), tol=1e-6,
+                   max_iter=2000)
+    Om = r["Omega"].cpu().numpy()
+    assert np.all(Om[1] == 0.0) and r["iters"][1] == 0
+    res = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om[:1].T, B[:1].T)
+    assert res.max() <= 1e-4
+
+
+def test_mbcg_reports_notconv(gp, ctx, w2k):
+    w = w2k
+    X = torch.from_numpy(w.X).cuda()
+    B = torch.from_numpy(w.y[None, :].copy()).cuda()
+    r = gp.gp_mbcg(ctx, X, _theta(gp, w), None, B, tol=1e-12, max_iter=2)
+    assert r["rc"] == gp.GP_ENOTCONV and r["iters"][0] == 2
+
+
+# --------------------------------------------------- log ML and gradient ----
+def test_logml_logdet_and_grad_gp2k(gp, ctx, w2k):
+    w = w2k
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(w.y).cuda()
+    seed, k, npr = 11, 32, 15
+    r = gp.gp_logml_and_grad(ctx, X, _theta(gp, w), y, n_probes=npr, seed=seed, k=k,
+                             tol=1e-6, max_iter=1000, allow_notconv=True)
+    Kh = go.khat_matrix(w.X, w.lengthscale, 1.0, w.sigma2)
+    L, _, _ = go.pivoted_cholesky(w.X, w.lengthscale, 1.0, k)
+    Zp = go.probe_vectors(L, w.sigma2, seed, npr)
+    tgt = go.same_probe_logdet_target(Kh, L, w.sigma2, Zp)
+    assert abs(r["logdet"] - tgt) <= 1e-3 * abs(tgt)
+    yd = w.y.astype(np.float64)
+    yKy = yd @ go.cholesky_solve(Kh, yd)
+    logml_tgt = go.log_marginal_likelihood(yKy, tgt, w.N)
+    assert abs(r["logml"] - logml_tgt) <= 1e-3 * abs(logml_tgt)
+    g_ref = go.same_probe_grad(w.X, yd, w.lengthscale, 1.0, w.sigma2, Zp,
+                               go.precond_solve(L, w.sigma2, Zp))
+    g = r["grad"]
+    assert np.abs(g - g_ref).max() <= 1e-3 * np.abs(g_ref).max()
+    # the outputscale and noise components individually
+    assert abs(g[-1] - g_ref[-1]) <= 1e-3 * abs(g_ref[-1])
+    assert abs(g[-2] - g_ref[-2]) <= 1e-3 * abs(g_ref[-2]) + 1e-3 * np.abs(g_ref).max()
+
+
+def test_autograd_function(gp, ctx):
+    w = make_workload("gp2k", N=300, d=4)
+    ell = torch.tensor(w.lengthscale, dtype=torch.float64, requires_grad=True)
+    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    sig2 = torch.tensor(w.sigma2, dtype=torch.float64, requires_grad=True)
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(w.y).cuda()
+    out = gp.MarginalLikelihood.apply(ell, s, sig2, X, y, ctx,
+                                      dict(n_probes=8, seed=1, k=8, tol=1e-6))
+    (-out).backward()
+    r = gp.gp_logml_and_grad(ctx, X, _theta(gp, w), y, n_probes=8, seed=1, k=8, tol=1e-6)
+    np.testing.assert_allclose(-ell.grad.numpy(), r["grad"][:4], rtol=1e-12)
+    assert math.isclose(-s.grad.item(), r["grad"][4], rel_tol=1e-12)
+    assert math.isclose(-sig2.grad.item(), r["grad"][5], rel_tol=1e-12)
+
+
+# ------------------------------------------------------------- prediction ----
+def test_predict_mean_and_variance(gp, ctx, w2k):
+    w = w2k
+    X = torch.from_numpy(w.X).cuda()
+    m = gp.gp_model_fit(ctx, X, _theta(gp, w), torch.from_numpy(w.y).cuda(), k=32, tol=1e-6)
+    Xt = torch.from_numpy(w.Xtest).cuda()
+    mean, var = gp.gp_predict(ctx, m, Xt, gp.GP_VAR_EXACT)
+    mr, vr = go.predict(w.X, w.y.astype(np.float64), w.Xtest, w.lengthscale, 1.0, w.sigma2)
+    assert _relerr(mean.cpu().numpy()[:, None], mr[:, None]) <= 1e-4
+    np.testing.assert_allclose(var.cpu().numpy(), vr, atol=1e-4)
+    m.free()
+
+
+# ----------------------------------------------------------- error paths ----
+def test_invalid_arguments_are_rejected(gp, ctx):
+    X = torch.zeros((4, 2), device="cuda")
+    V = torch.zeros((1, 4), device="cuda")
+    with pytest.raises(gp.GPError, match="GP_EINVAL"):
+        gp.gp_kmatmul(ctx, X, gp.Theta(np.array([1.0, -1.0])), V)
+    with pytest.raises(gp.GPError, match="GP_EINVAL"):
+        gp.gp_kmatmul(ctx, X, gp.Theta(np.array([1.0, 1.0]), 1.0, 0.0), V)
+    with pytest.raises(gp.GPError, match="GP_EINVAL"):
+        gp.gp_kmatmul(ctx, X, gp.Theta(np.ones(2)), V, precision=9)
