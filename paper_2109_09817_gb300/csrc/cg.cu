@@ -505,6 +505,7 @@ int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res) {
     GP_LAUNCHED(ctx);
     GP_CUDA(ctx, cudaMemcpyAsync(flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    GP_TRY(check_status(ctx));
     res->iters_max = it + 1;
     if (flags[1]) {
       res->breakdown = true;

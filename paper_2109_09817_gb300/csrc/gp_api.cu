@@ -179,6 +179,7 @@ void gp_destroy(gp_ctx* ctx) {
   for (auto& b : ctx->ws)
     if (b.p) cudaFree(b.p);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->status_host) cudaFreeHost(ctx->status_host);
   delete ctx;
 }
 
@@ -192,7 +193,7 @@ int gp_set_stream(gp_ctx* ctx, void* stream) {
 int gp_sync(gp_ctx* ctx) {
   if (!ctx) return GP_EINVAL;
   GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return GP_OK;
+  return check_status(ctx);
 }
 
 const char* gp_last_error(const gp_ctx* ctx) {

@@ -43,7 +43,7 @@ enum WsSlot {
   WS_PC_L, WS_PC_L32, WS_PC_D, WS_PC_PIV, WS_PC_STATE, WS_PC_GRAM, WS_PC_CF,
   WS_LZ_SCR, WS_LZ_OUT,
   WS_GR_U, WS_GR_W, WS_GR_ACC,
-  WS_PR_K, WS_PR_O,
+  WS_PR_K, WS_PR_O, WS_STATUS,
   WS_COUNT
 };
 
@@ -68,6 +68,8 @@ struct gp_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t ev_used = 0;
   double prof_flops = 0.0, prof_elems = 0.0;
+  bool status_init = false;      // device status word (bounded-wait timeouts)
+  int* status_host = nullptr;    // its own pinned word (never the staging area)
 };
 
 namespace gp {
@@ -138,6 +140,11 @@ int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V,
            int64_t ldv, int t, float* out, int64_t ldo, float s, bool sym,
            int precision);
 bool kmv_tc_supported(const Prep& rows, int t, int precision);
+// Device status word written by kernels whose waits are bounded (0 = ok,
+// GP_ETIMEOUT = a wait gave up).  check_status synchronises, returns the
+// recorded code as a gp error and clears it.
+int* device_status(gp_ctx* ctx);
+int check_status(gp_ctx* ctx);
 // out = sigma2 * V (sym) or 0, rows of length n
 int kmv_init_out(gp_ctx* ctx, const float* V, int64_t ldv, int t, int64_t n,
                  float* out, int64_t ldo, float sigma2);

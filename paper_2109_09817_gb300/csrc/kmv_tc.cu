@@ -1,14 +1,695 @@
-// Tensor-core K-hat V (tcgen05): not built yet; every precision other than
-// GP_FP32_PLAIN reports GP_EINVAL through kmv().
+// Tensor-core K-hat V on sm_103a (tcgen05 + TMEM + TMA), split-TF32.
+//
+// arXiv 2109.09817 Sec. 3.1-3.2 (blackbox products with K-hat, O(N)
+// memory) and Sec. 4 (kernel tiles).  Per CTA: a 128-row tile I and a range
+// of 64-column tiles J.  Per J tile:
+//   MMA1  S = X~_I X~_J^T          tcgen05.mma kind::tf32, operands in 128B-
+//                                  swizzled SMEM (TMA), accumulator in TMEM;
+//                                  split: S = hi.hi^T + hi.lo^T + lo.hi^T
+//   epi   K = matern(n_a + n_b - 2S) on the FP32/MUFU pipes (8 warps), written
+//         back to TMEM as K_hi (over S) and K_lo = tf32(K - K_hi)
+//   MMA2  O_J = K_hi V_hi + K_hi V_lo + K_lo V_hi    (A operand from TMEM)
+//   epi   O_J drained from TMEM and added into per-thread registers with a
+//         compensated (Kahan) sum; flushed once per CTA with atomics.
+// S/K and O are double-buffered in TMEM so that the MMAs of one tile overlap
+// the epilogue of the next.  Warp roles: 0 TMA producer, 1 MMA issuer,
+// 2 TMEM allocator, 4..11 epilogue.  Every mbarrier wait is bounded: on a
+// timeout the kernel records GP_ETIMEOUT in a status word and all roles
+// leave their loops.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "gp_internal.cuh"
 
 namespace gp {
+namespace {
 
-bool kmv_tc_supported(const Prep&, int, int) { return false; }
+constexpr int BM = 128;
+constexpr int BN = 64;
+constexpr int NTHREADS = 640;     // 4 control warps + 2 x 8 epilogue warps
+constexpr int EPI_WARP0 = 4;
+constexpr int GROUP_WARPS = 8;    // one epilogue group: 2 warps per TMEM lane quarter
+constexpr int OGROUP = 2;         // a group's J tiles accumulated in TMEM per O drain
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
-int kmv_tc(gp_ctx* ctx, const Prep&, const Prep&, const float*, int64_t, int,
-           float*, int64_t, float, bool, int) {
-  return set_err(ctx, GP_EINVAL, "tensor-core product not available");
+// ---------------------------------------------------------------- PTX --------
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on timeout or when another role already failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* fail) {
+  if (mbar_test(b, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_test(b, parity)) return true;
+    if ((i & 255) == 0) {
+      if (*reinterpret_cast<volatile int*>(fail)) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        atomicExch(fail, 1);
+        return false;
+      }
+    }
+  }
+}
+// Bounded wait used on the way out (ignores the failure flag).
+__device__ __forceinline__ bool mbar_wait_exit(uint64_t* b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(b, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          su32(dst)),
+      "l"(map), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// SMEM matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor: kind::tf32, D = F32, A and B K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+[[maybe_unused]] __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+}
+[[maybe_unused]] __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------------- layout ------
+template <int DP, int T>
+struct TcLayout {
+  static constexpr int KB = DP / 32;                   // 128-byte K boxes of X~
+  static constexpr int STAGES = DP <= 32 ? 4 : 3;
+  static constexpr int A_BOX = BM * 128;               // bytes per K box, A
+  static constexpr int XJ_BOX = BN * 128;              // bytes per K box, X~_J
+  static constexpr int V_BOX = T * 128;                // bytes per K box of V_J
+  static constexpr int A_HI = 0;
+  static constexpr int A_LO = A_HI + KB * A_BOX;
+  static constexpr int ST0 = A_LO + KB * A_BOX;
+  static constexpr int S_XHI = 0;
+  static constexpr int S_XLO = S_XHI + KB * XJ_BOX;
+  static constexpr int S_VHI = S_XLO + KB * XJ_BOX;
+  static constexpr int S_VLO = S_VHI + 2 * V_BOX;
+  static constexpr int S_NRM = S_VLO + 2 * V_BOX;
+  static constexpr int STAGE_BYTES = (S_NRM + 256 + 1023) / 1024 * 1024;
+  static constexpr int BAR = ST0 + STAGES * STAGE_BYTES;
+  static constexpr int NBAR = 1 + 2 * STAGES + 4 + 8 + 1;
+  static constexpr int TOTAL = BAR + NBAR * 8 + 16;
+  static constexpr uint32_t TX_A = 2u * KB * A_BOX;
+  static constexpr uint32_t TX_STAGE = 2u * KB * XJ_BOX + 4u * V_BOX + 256u;
+  // TMEM columns
+  // per S buffer b: [b*128, +64) the hi.hi product, then K_hi;
+  //                 [b*128+64, +64) the hi.lo + lo.hi products, then K_lo
+  static constexpr uint32_t T_S = 0;
+  static constexpr uint32_t T_X = 64;
+  static constexpr uint32_t T_O = 256;      // 2 epilogue groups x 2 x T: O
+  static constexpr uint32_t T_COLS = 512;
+};
+
+struct TcParams {
+  const float* nr;      // row norms (padded)
+  const float* nc;      // column norms (padded)
+  int64_t nrows, ncols;
+  float* out;
+  int64_t ldo;
+  int t;                // live vectors in this chunk
+  float s;
+  int sym;
+  int tiles_per_split;
+  int split;            // 1: hi/lo products, 0: single tf32 product
+  int* status;
+};
+
+template <int DP, int T>
+__global__ void __launch_bounds__(NTHREADS, 1)
+kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constant__ CUtensorMap map_r_lo,
+              const __grid_constant__ CUtensorMap map_c_hi, const __grid_constant__ CUtensorMap map_c_lo,
+              const __grid_constant__ CUtensorMap map_v_hi, const __grid_constant__ CUtensorMap map_v_lo,
+              const TcParams p) {
+  using Ly = TcLayout<DP, T>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Ly::BAR);
+  uint64_t* bar_a = bars;
+  uint64_t* bar_full = bars + 1;                    // [STAGES]
+  uint64_t* bar_empty = bar_full + Ly::STAGES;      // [STAGES]
+  uint64_t* bar_s = bar_empty + Ly::STAGES;         // [2]    S of group g ready
+  uint64_t* bar_k = bar_s + 2;                      // [2]    K of group g written
+  uint64_t* bar_of = bar_k + 2;                     // [2][2] O of group g, buffer u ready
+  uint64_t* bar_oe = bar_of + 4;                    // [2][2] ... drained
+  uint64_t* bar_fin = bar_oe + 4;                   // MMA pipeline drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + Ly::NBAR);
+  __shared__ int fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int64_t n_col_tiles = (p.ncols + BN - 1) / BN;
+  const int64_t jt0 = (int64_t)blockIdx.y * p.tiles_per_split;
+  const int64_t jt1 = min(n_col_tiles, jt0 + (int64_t)p.tiles_per_split);
+  const int ntiles = (int)(jt1 - jt0);
+  if (ntiles <= 0) return;
+
+  if (threadIdx.x == 0) {
+    fail = 0;
+    mbar_init(bar_a, 1);
+    for (int i = 0; i < Ly::STAGES; ++i) {
+      mbar_init(bar_full + i, 1);
+      mbar_init(bar_empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar_s + i, 1);
+      mbar_init(bar_k + i, GROUP_WARPS);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(bar_of + i, 1);
+      mbar_init(bar_oe + i, GROUP_WARPS);
+    }
+    mbar_init(bar_fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(Ly::T_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------- TMA producer --
+    mbar_expect_tx(bar_a, Ly::TX_A);
+    for (int kb = 0; kb < Ly::KB; ++kb) {
+      tma_2d(smem + Ly::A_HI + kb * Ly::A_BOX, &map_r_hi, bar_a, kb * 32, (int)row0);
+      tma_2d(smem + Ly::A_LO + kb * Ly::A_BOX, p.split ? &map_r_lo : &map_r_hi, bar_a, kb * 32, (int)row0);
+    }
+    int armed = 0;   // tiles whose loads have been issued
+    for (int j = 0; j < ntiles; ++j) {
+      const int st = j % Ly::STAGES;
+      if (j >= Ly::STAGES) {
+        if (!mbar_wait(bar_empty + st, ((j / Ly::STAGES) - 1) & 1, &fail)) break;
+      }
+      uint8_t* sb = smem + Ly::ST0 + st * Ly::STAGE_BYTES;
+      const int col0 = (int)((jt0 + j) * BN);
+      mbar_expect_tx(bar_full + st, Ly::TX_STAGE);
+      for (int kb = 0; kb < Ly::KB; ++kb) {
+        tma_2d(sb + Ly::S_XHI + kb * Ly::XJ_BOX, &map_c_hi, bar_full + st, kb * 32, col0);
+        tma_2d(sb + Ly::S_XLO + kb * Ly::XJ_BOX, p.split ? &map_c_lo : &map_c_hi, bar_full + st, kb * 32, col0);
+      }
+      for (int vb = 0; vb < 2; ++vb) {
+        tma_2d(sb + Ly::S_VHI + vb * Ly::V_BOX, &map_v_hi, bar_full + st, col0 + vb * 32, 0);
+        tma_2d(sb + Ly::S_VLO + vb * Ly::V_BOX, p.split ? &map_v_lo : &map_v_hi, bar_full + st, col0 + vb * 32, 0);
+      }
+      bulk_g2s(sb + Ly::S_NRM, p.nc + col0, 256, bar_full + st);
+      armed = j + 1;
+    }
+    // never leave with bulk copies still landing in this CTA's memory
+    mbar_wait_exit(bar_a, 0);
+    for (int j = max(0, armed - Ly::STAGES); j < armed; ++j)
+      mbar_wait_exit(bar_full + (j % Ly::STAGES), (j / Ly::STAGES) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer --
+    // Tile j belongs to epilogue group g = j & 1 (S/K buffer g), its i-th
+    // tile with i = j >> 1; the group's O accumulates OGROUP of its tiles in
+    // buffer u = (i / OGROUP) & 1.
+    constexpr uint32_t ID1 = idesc_tf32(BM, BN);
+    constexpr uint32_t ID2 = idesc_tf32(BM, T);
+    const uint32_t a_hi = su32(smem + Ly::A_HI), a_lo = su32(smem + Ly::A_LO);
+    bool ok = mbar_wait(bar_a, 0, &fail);
+    fence_after();
+    // S_hh = A_hi B_hi^T into [g*128, +64); S_x = A_hi B_lo^T + A_lo B_hi^T
+    // into [g*128+64, +64): the large product accumulates on its own
+    auto mma1 = [&](int j, int buf) {
+      const int st = j % Ly::STAGES;
+      const uint32_t sb = su32(smem + Ly::ST0 + st * Ly::STAGE_BYTES);
+      const uint32_t dhh = tbase + Ly::T_S + buf * 128;
+      const uint32_t dx = dhh + Ly::T_X;
+      for (int kk = 0; kk < DP / 8; ++kk) {
+        const uint32_t ko = (kk & 3) * 32;   // 8 tf32 = 32 B inside a 128 B atom
+        const uint32_t aoff = (kk >> 2) * Ly::A_BOX + ko;
+        const uint32_t boff = (kk >> 2) * Ly::XJ_BOX + ko;
+        mma_ss(dhh, sdesc(a_hi + aoff), sdesc(sb + Ly::S_XHI + boff), ID1, kk ? 1u : 0u);
+        if (p.split) {
+          mma_ss(dx, sdesc(a_hi + aoff), sdesc(sb + Ly::S_XLO + boff), ID1, kk ? 1u : 0u);
+          mma_ss(dx, sdesc(a_lo + aoff), sdesc(sb + Ly::S_XHI + boff), ID1, 1u);
+        }
+      }
+    };
+    // O += K_hi V_hi + K_hi V_lo + K_lo V_hi (A from TMEM)
+    auto mma2 = [&](int j, int buf, uint32_t ocol, bool first) {
+      const int st = j % Ly::STAGES;
+      const uint32_t sb = su32(smem + Ly::ST0 + st * Ly::STAGE_BYTES);
+      const uint32_t d = tbase + ocol;
+      const uint32_t khi = tbase + Ly::T_S + buf * 128, klo = khi + Ly::T_X;
+      for (int kk = 0; kk < BN / 8; ++kk) {
+        const uint32_t boff = (kk >> 2) * Ly::V_BOX + (kk & 3) * 32;
+        mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_VHI + boff), ID2, (first && kk == 0) ? 0u : 1u);
+        if (p.split) {
+          mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_VLO + boff), ID2, 1u);
+          mma_ts(d, klo + kk * 8, sdesc(sb + Ly::S_VHI + boff), ID2, 1u);
+        }
+      }
+    };
+    for (int j = 0; ok && j < 2 && j < ntiles; ++j) {
+      if (!(ok = mbar_wait(bar_full + (j % Ly::STAGES), (j / Ly::STAGES) & 1, &fail))) break;
+      fence_after();
+      mma1(j, j & 1);
+      mma_commit(bar_s + (j & 1));
+    }
+    for (int j = 0; ok && j < ntiles; ++j) {
+      const int g = j & 1, i = j >> 1;
+      const int og = i / OGROUP, u = og & 1;
+      const bool first = (i % OGROUP) == 0;
+      const bool last = (i % OGROUP) == OGROUP - 1 || j + 2 >= ntiles;
+      if (!(ok = mbar_wait(bar_k + g, i & 1, &fail))) break;
+      fence_after();
+      if (first && og >= 2) {
+        if (!(ok = mbar_wait(bar_oe + 2 * g + u, ((og - 2) >> 1) & 1, &fail))) break;
+        fence_after();
+      }
+      mma2(j, g, Ly::T_O + (2 * g + u) * T, first);
+      if (last) mma_commit(bar_of + 2 * g + u);
+      mma_commit(bar_empty + (j % Ly::STAGES));
+      if (j + 2 < ntiles) {
+        const int j2 = j + 2;
+        if (!(ok = mbar_wait(bar_full + (j2 % Ly::STAGES), (j2 / Ly::STAGES) & 1, &fail))) break;
+        fence_after();
+        mma1(j2, g);
+        mma_commit(bar_s + g);
+      }
+    }
+    // every MMA issued above has completed before TMEM is released
+    mma_commit(bar_fin);
+    mbar_wait_exit(bar_fin, 0);
+  } else if (warp >= EPI_WARP0) {
+    // ----------------------------------------------------------- epilogue --
+    const int e = warp - EPI_WARP0;
+    const int g = e / GROUP_WARPS;       // epilogue group: tiles j with j & 1 == g
+    const int q = warp & 3;              // TMEM lane quarter of this warp
+    const int h = (e % GROUP_WARPS) >> 2;  // column half (32 columns)
+    const int r = q * 32 + lane;         // row within the tile
+    const int64_t grow = row0 + r;
+    const float na = p.nr[grow];
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int my_tiles = (ntiles - g + 1) / 2;   // tiles j = g, g + 2, ...
+    constexpr int TH = T / 2;            // O columns drained by this warp
+    float acc[TH], cmp[TH];
+#pragma unroll
+    for (int c = 0; c < TH; ++c) {
+      acc[c] = 0.f;
+      cmp[c] = 0.f;
+    }
+    auto drain = [&](int og) -> bool {
+      const int u = og & 1;
+      if (!mbar_wait(bar_of + 2 * g + u, (og >> 1) & 1, &fail)) return false;
+      fence_after();
+      float v[TH];
+      const uint32_t oa = tbase + lane_off + Ly::T_O + (2 * g + u) * T + h * TH;
+      if constexpr (TH == 8) {
+        uint32_t rr[8];
+        tmem_ld8(oa, rr);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(rr[c]);
+      } else {
+        uint32_t rr[16];
+        tmem_ld16(oa, rr);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(rr[c]);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_oe + 2 * g + u);
+#pragma unroll
+      for (int c = 0; c < TH; ++c) {
+        const float yv = v[c] - cmp[c];
+        const float tv = acc[c] + yv;
+        cmp[c] = (tv - acc[c]) - yv;
+        acc[c] = tv;
+      }
+      return true;
+    };
+    bool ok = true;
+    for (int i = 0; i < my_tiles; ++i) {
+      const int j = 2 * i + g;
+      const int st = j % Ly::STAGES;
+      const int64_t col0 = (jt0 + j) * BN;
+      if (!(ok = mbar_wait(bar_s + g, i & 1, &fail))) break;
+      // the stage's norms: its load completed before MMA1 was issued; the
+      // wait makes the async-proxy writes visible to this thread
+      if (!(ok = mbar_wait(bar_full + st, (j / Ly::STAGES) & 1, &fail))) break;
+      fence_after();
+      const bool diag = p.sym && row0 < col0 + BN && col0 < row0 + BM;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int cb = h * 32 + half * 16;   // first of these 16 columns
+        const float4* snb =
+            reinterpret_cast<const float4*>(smem + Ly::ST0 + st * Ly::STAGE_BYTES + Ly::S_NRM) + cb / 4;
+        const uint32_t sa = tbase + lane_off + Ly::T_S + g * 128 + cb;
+        uint32_t sh[16], sx[16];
+        tmem_ld16(sa, sh);
+        if (p.split) tmem_ld16(sa + Ly::T_X, sx);
+        float nb[16];
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const float4 v4 = snb[c4];
+          nb[4 * c4 + 0] = v4.x;
+          nb[4 * c4 + 1] = v4.y;
+          nb[4 * c4 + 2] = v4.z;
+          nb[4 * c4 + 3] = v4.w;
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          float sab = __uint_as_float(sh[c]);
+          if (p.split) sab += __uint_as_float(sx[c]);
+          const float u2 = fmaxf(fmaf(-2.f, sab, na + nb[c]), 0.f);
+          const float uu = sqrt_approx(u2);
+          const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
+          // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder
+          // (|lo| <= 2^-11 |K|, so kind::tf32 reading lo costs <= 2^-22 |K|)
+          const float hi = tf32_rna(kv);
+          sh[c] = __float_as_uint(hi);
+          sx[c] = __float_as_uint(kv - hi);
+        }
+        if (diag) {
+          // diagonal tile: the entry a = b is exactly k(0) = 1
+          const int64_t dc = grow - (col0 + cb);
+          const uint32_t dmask = (dc >= 0 && dc < 16) ? (1u << (int)dc) : 0u;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const bool on = (dmask >> c) & 1u;
+            sh[c] = on ? __float_as_uint(1.0f) : sh[c];
+            sx[c] = on ? 0u : sx[c];
+          }
+        }
+        tmem_st16(sa, sh);
+        if (p.split) tmem_st16(sa + Ly::T_X, sx);
+      }
+      tmem_wait_st();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_k + g);
+      // drain this group's previous O buffer once its last MMA2 was issued
+      if ((i % OGROUP) == 0 && i > 0 && !(ok = drain(i / OGROUP - 1))) break;
+    }
+    if (ok && my_tiles > 0) ok = drain((my_tiles - 1) / OGROUP);
+    if (ok && my_tiles > 0 && grow < p.nrows) {
+#pragma unroll
+      for (int c = 0; c < TH; ++c) {
+        const int col = h * TH + c;
+        if (col < p.t) atomicAdd(p.out + (int64_t)col * p.ldo + grow, p.s * (acc[c] - cmp[c]));
+      }
+    }
+  }
+  // ------------------------------------------------------------- teardown --
+  fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(Ly::T_COLS)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && fail) atomicExch(p.status, GP_ETIMEOUT);
+}
+
+// V (t vectors, ld ldv, n valid) -> hi/lo TF32 parts, T_pad vectors of
+// length n_pad (zero padding).
+__global__ void split_v_kernel(const float* __restrict__ V, int64_t ldv, int t, int64_t n,
+                               int tpad, int64_t npad, float* __restrict__ vhi,
+                               float* __restrict__ vlo) {
+  const int64_t total = (int64_t)tpad * npad;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / npad, a = i % npad;
+    const float v = (c < t && a < n) ? V[c * ldv + a] : 0.f;
+    const float h = tf32_rna(v);
+    vhi[i] = h;
+    vlo[i] = tf32_rna(v - h);
+  }
+}
+
+// ------------------------------------------------------------- host side ----
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D FP32 tensor [rows][cols] (cols contiguous), box = 32 cols x box_rows,
+// 128-byte swizzle.
+int make_map(gp_ctx* ctx, CUtensorMap* m, const float* base, int64_t rows, int64_t cols,
+             int64_t ld, int box_rows, int box_cols = 32, bool swizzle = true) {
+  auto fn = encode_fn();
+  if (!fn) return set_err(ctx, GP_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstr[1] = {(cuuint64_t)ld * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1u, 1u};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstr, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_err(ctx, GP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return GP_OK;
+}
+
+template <int DP, int T>
+int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi, const float* vlo,
+              int64_t vld, int t, float* out, int64_t ldo, float s, bool sym, bool split, int* status) {
+  using Ly = TcLayout<DP, T>;
+  CUtensorMap mrh, mrl, mch, mcl, mvh, mvl;
+  const float* rlo = split ? rows.xt_lo : rows.xt_hi;
+  const float* clo = split ? cols.xt_lo : cols.xt_hi;
+  GP_TRY(make_map(ctx, &mrh, rows.xt_hi, rows.n_pad, DP, DP, BM));
+  GP_TRY(make_map(ctx, &mrl, rlo, rows.n_pad, DP, DP, BM));
+  GP_TRY(make_map(ctx, &mch, cols.xt_hi, cols.n_pad, DP, DP, BN));
+  GP_TRY(make_map(ctx, &mcl, clo, cols.n_pad, DP, DP, BN));
+  GP_TRY(make_map(ctx, &mvh, vhi, T, cols.n_pad, vld, T));
+  GP_TRY(make_map(ctx, &mvl, split ? vlo : vhi, T, cols.n_pad, vld, T));
+  const size_t smem = Ly::TOTAL + 1024;
+  static bool attr = false;
+  if (!attr) {
+    GP_CUDA(ctx, cudaFuncSetAttribute(kmv_tc_kernel<DP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    attr = true;
+  }
+  const int64_t row_tiles = ceil_div(rows.n, BM);
+  const int64_t col_tiles = ceil_div(cols.n, BN);
+  int64_t splits = std::max<int64_t>(1, ceil_div(4LL * ctx->num_sms, row_tiles));
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, col_tiles / 4));
+  const int64_t per = ceil_div(col_tiles, splits);
+  splits = ceil_div(col_tiles, per);
+  TcParams prm;
+  prm.nr = rows.norm;
+  prm.nc = cols.norm;
+  prm.nrows = rows.n;
+  prm.ncols = cols.n;
+  prm.out = out;
+  prm.ldo = ldo;
+  prm.t = t;
+  prm.s = s;
+  prm.sym = sym ? 1 : 0;
+  prm.tiles_per_split = (int)per;
+  prm.split = split ? 1 : 0;
+  prm.status = status;
+  kmv_tc_kernel<DP, T><<<dim3((unsigned)row_tiles, (unsigned)splits), NTHREADS, smem, ctx->stream>>>(
+      mrh, mrl, mch, mcl, mvh, mvl, prm);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+}  // namespace
+
+bool kmv_tc_supported(const Prep& rows, int t, int precision) {
+  (void)t;
+  if (precision != GP_FP32_SPLIT_TF32 && precision != GP_TF32) return false;
+  return rows.d_pad == 32 || rows.d_pad == 64;
+}
+
+int* device_status(gp_ctx* ctx) {
+  int* st = static_cast<int*>(ws_get(ctx, WS_STATUS, 64));
+  if (st && !ctx->status_init) {
+    if (cudaMemsetAsync(st, 0, 64, ctx->stream) != cudaSuccess) return nullptr;
+    ctx->status_init = true;
+  }
+  return st;
+}
+
+int check_status(gp_ctx* ctx) {
+  if (!ctx->status_init) return GP_OK;
+  int* st = static_cast<int*>(ws_get(ctx, WS_STATUS, 64));
+  if (!ctx->status_host && cudaMallocHost(&ctx->status_host, 64) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->status_host = nullptr;
+  }
+  int* h = ctx->status_host;
+  if (!st || !h) return set_err(ctx, GP_ENOMEM, "status readback");
+  GP_CUDA(ctx, cudaMemcpyAsync(h, st, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int code = h[0];
+  if (code != 0) {
+    GP_CUDA(ctx, cudaMemsetAsync(st, 0, 64, ctx->stream));
+    return set_err(ctx, code, "a tensor-core K-hat V wait timed out (status %d)", code);
+  }
+  return GP_OK;
+}
+
+int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V, int64_t ldv, int t,
+           float* out, int64_t ldo, float s, bool sym, int precision) {
+  const bool split = precision == GP_FP32_SPLIT_TF32;
+  if (!rows.xt_hi || !cols.xt_hi) return set_err(ctx, GP_EINVAL, "tensor-core features not prepared");
+  int* status = device_status(ctx);
+  if (!status) return set_err(ctx, GP_ENOMEM, "workspace (status)");
+  const int64_t npad = cols.n_pad;
+  for (int c0 = 0; c0 < t; c0 += 32) {
+    const int tc = std::min(32, t - c0);
+    const int T = tc <= 16 ? 16 : 32;
+    float* vhi = ws<float>(ctx, WS_VHI, (size_t)T * npad);
+    float* vlo = ws<float>(ctx, WS_VLO, (size_t)T * npad);
+    if (!vhi || !vlo) return set_err(ctx, GP_ENOMEM, "workspace (V split)");
+    const int64_t total = (int64_t)T * npad;
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 16LL * ctx->num_sms);
+    split_v_kernel<<<g, 256, 0, ctx->stream>>>(V + (int64_t)c0 * ldv, ldv, tc, cols.n, T, npad, vhi, vlo);
+    GP_LAUNCHED(ctx);
+    float* oc = out + (int64_t)c0 * ldo;
+    int rc;
+    if (rows.d_pad == 32)
+      rc = T == 16 ? launch_tc<32, 16>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status)
+                   : launch_tc<32, 32>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status);
+    else
+      rc = T == 16 ? launch_tc<64, 16>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status)
+                   : launch_tc<64, 32>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status);
+    if (rc != GP_OK) return rc;
+  }
+  return GP_OK;
 }
 
 }  // namespace gp
