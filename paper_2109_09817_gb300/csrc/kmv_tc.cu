@@ -201,11 +201,11 @@ struct TcLayout {
   static constexpr int A_HI = 0;
   static constexpr int A_LO = A_HI + KB * A_BOX;
   static constexpr int ST0 = A_LO + KB * A_BOX;
-  static constexpr int S_XHI = 0;
-  static constexpr int S_XLO = S_XHI + KB * XJ_BOX;
-  static constexpr int S_VHI = S_XLO + KB * XJ_BOX;
-  static constexpr int S_VLO = S_VHI + 2 * V_BOX;
-  static constexpr int S_NRM = S_VLO + 2 * V_BOX;
+  // per 128-byte K box kb of X~_J: [hi rows 0..63][lo rows 0..63], so that
+  // hi and lo stack into one N = 128 B operand; likewise V_J: [hi T rows][lo T rows]
+  static constexpr int S_X = 0;                        // + kb * 2 * XJ_BOX (+ XJ_BOX for lo)
+  static constexpr int S_V = S_X + KB * 2 * XJ_BOX;    // + vb * 2 * V_BOX (+ V_BOX for lo)
+  static constexpr int S_NRM = S_V + 2 * 2 * V_BOX;
   static constexpr int STAGE_BYTES = (S_NRM + 256 + 1023) / 1024 * 1024;
   static constexpr int BAR = ST0 + STAGES * STAGE_BYTES;
   static constexpr int NBAR = 1 + 2 * STAGES + 4 + 8 + 1;
@@ -217,7 +217,7 @@ struct TcLayout {
   //                 [b*128+64, +64) the hi.lo + lo.hi products, then K_lo
   static constexpr uint32_t T_S = 0;
   static constexpr uint32_t T_X = 64;
-  static constexpr uint32_t T_O = 256;      // 2 epilogue groups x 2 x T: O
+  static constexpr uint32_t T_O = 256;      // 2 epilogue groups x 2 x 2T: O (hh | hi.lo part)
   static constexpr uint32_t T_COLS = 512;
 };
 
@@ -312,12 +312,14 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       const int col0 = (int)((jt0 + j) * BN);
       mbar_expect_tx(bar_full + st, Ly::TX_STAGE);
       for (int kb = 0; kb < Ly::KB; ++kb) {
-        tma_2d(sb + Ly::S_XHI + kb * Ly::XJ_BOX, &map_c_hi, bar_full + st, kb * 32, col0);
-        tma_2d(sb + Ly::S_XLO + kb * Ly::XJ_BOX, p.split ? &map_c_lo : &map_c_hi, bar_full + st, kb * 32, col0);
+        tma_2d(sb + Ly::S_X + (2 * kb) * Ly::XJ_BOX, &map_c_hi, bar_full + st, kb * 32, col0);
+        tma_2d(sb + Ly::S_X + (2 * kb + 1) * Ly::XJ_BOX, p.split ? &map_c_lo : &map_c_hi, bar_full + st,
+               kb * 32, col0);
       }
       for (int vb = 0; vb < 2; ++vb) {
-        tma_2d(sb + Ly::S_VHI + vb * Ly::V_BOX, &map_v_hi, bar_full + st, col0 + vb * 32, 0);
-        tma_2d(sb + Ly::S_VLO + vb * Ly::V_BOX, p.split ? &map_v_lo : &map_v_hi, bar_full + st, col0 + vb * 32, 0);
+        tma_2d(sb + Ly::S_V + (2 * vb) * Ly::V_BOX, &map_v_hi, bar_full + st, col0 + vb * 32, 0);
+        tma_2d(sb + Ly::S_V + (2 * vb + 1) * Ly::V_BOX, p.split ? &map_v_lo : &map_v_hi, bar_full + st,
+               col0 + vb * 32, 0);
       }
       bulk_g2s(sb + Ly::S_NRM, p.nc + col0, 256, bar_full + st);
       armed = j + 1;
@@ -331,13 +333,18 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
     // Tile j belongs to epilogue group g = j & 1 (S/K buffer g), its i-th
     // tile with i = j >> 1; the group's O accumulates OGROUP of its tiles in
     // buffer u = (i / OGROUP) & 1.
-    constexpr uint32_t ID1 = idesc_tf32(BM, BN);
+    constexpr uint32_t ID1 = idesc_tf32(BM, BN);          // N = 64
+    constexpr uint32_t ID1W = idesc_tf32(BM, 2 * BN);     // N = 128: [hi; lo] stacked
     constexpr uint32_t ID2 = idesc_tf32(BM, T);
+    constexpr uint32_t ID2W = idesc_tf32(BM, 2 * T);
     const uint32_t a_hi = su32(smem + Ly::A_HI), a_lo = su32(smem + Ly::A_LO);
     bool ok = mbar_wait(bar_a, 0, &fail);
     fence_after();
-    // S_hh = A_hi B_hi^T into [g*128, +64); S_x = A_hi B_lo^T + A_lo B_hi^T
-    // into [g*128+64, +64): the large product accumulates on its own
+    // Columns [g*128, +64) get A_hi B_hi^T and [g*128+64, +64) get
+    // A_hi B_lo^T + A_lo B_hi^T: one N = 128 MMA writes both halves
+    // (B = [hi; lo] rows), a second N = 64 MMA adds A_lo B_hi^T.  Every
+    // tcgen05.mma costs a roughly fixed time at small N, so products are
+    // stacked along N rather than issued separately.
     auto mma1 = [&](int j, int buf) {
       const int st = j % Ly::STAGES;
       const uint32_t sb = su32(smem + Ly::ST0 + st * Ly::STAGE_BYTES);
@@ -346,26 +353,30 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       for (int kk = 0; kk < DP / 8; ++kk) {
         const uint32_t ko = (kk & 3) * 32;   // 8 tf32 = 32 B inside a 128 B atom
         const uint32_t aoff = (kk >> 2) * Ly::A_BOX + ko;
-        const uint32_t boff = (kk >> 2) * Ly::XJ_BOX + ko;
-        mma_ss(dhh, sdesc(a_hi + aoff), sdesc(sb + Ly::S_XHI + boff), ID1, kk ? 1u : 0u);
+        const uint32_t boff = (kk >> 2) * 2 * Ly::XJ_BOX + ko;
         if (p.split) {
-          mma_ss(dx, sdesc(a_hi + aoff), sdesc(sb + Ly::S_XLO + boff), ID1, kk ? 1u : 0u);
-          mma_ss(dx, sdesc(a_lo + aoff), sdesc(sb + Ly::S_XHI + boff), ID1, 1u);
+          mma_ss(dhh, sdesc(a_hi + aoff), sdesc(sb + Ly::S_X + boff), ID1W, kk ? 1u : 0u);
+          mma_ss(dx, sdesc(a_lo + aoff), sdesc(sb + Ly::S_X + boff), ID1, 1u);
+        } else {
+          mma_ss(dhh, sdesc(a_hi + aoff), sdesc(sb + Ly::S_X + boff), ID1, kk ? 1u : 0u);
         }
       }
     };
-    // O += K_hi V_hi + K_hi V_lo + K_lo V_hi (A from TMEM)
+    // O[0, T) += K_hi V_hi + K_lo V_hi and O[T, 2T) += K_hi V_lo: the first
+    // MMA stacks [V_hi; V_lo] along N (A from TMEM)
     auto mma2 = [&](int j, int buf, uint32_t ocol, bool first) {
       const int st = j % Ly::STAGES;
       const uint32_t sb = su32(smem + Ly::ST0 + st * Ly::STAGE_BYTES);
       const uint32_t d = tbase + ocol;
       const uint32_t khi = tbase + Ly::T_S + buf * 128, klo = khi + Ly::T_X;
       for (int kk = 0; kk < BN / 8; ++kk) {
-        const uint32_t boff = (kk >> 2) * Ly::V_BOX + (kk & 3) * 32;
-        mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_VHI + boff), ID2, (first && kk == 0) ? 0u : 1u);
+        const uint32_t boff = (kk >> 2) * 2 * Ly::V_BOX + (kk & 3) * 32;
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
         if (p.split) {
-          mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_VLO + boff), ID2, 1u);
-          mma_ts(d, klo + kk * 8, sdesc(sb + Ly::S_VHI + boff), ID2, 1u);
+          mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_V + boff), ID2W, acc);
+          mma_ts(d, klo + kk * 8, sdesc(sb + Ly::S_V + boff), ID2, 1u);
+        } else {
+          mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_V + boff), ID2, acc);
         }
       }
     };
@@ -386,7 +397,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
         if (!(ok = mbar_wait(bar_oe + 2 * g + u, ((og - 2) >> 1) & 1, &fail))) break;
         fence_after();
       }
-      mma2(j, g, Ly::T_O + (2 * g + u) * T, first);
+      mma2(j, g, Ly::T_O + (2 * g + u) * 2 * T, first);
       if (last) mma_commit(bar_of + 2 * g + u);
       mma_commit(bar_empty + (j % Ly::STAGES));
       if (j + 2 < ntiles) {
@@ -418,35 +429,31 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       acc[c] = 0.f;
       cmp[c] = 0.f;
     }
+    auto kahan = [&](int c, float v) {
+      const float yv = v - cmp[c];
+      const float tv = acc[c] + yv;
+      cmp[c] = (tv - acc[c]) - yv;
+      acc[c] = tv;
+    };
     auto drain = [&](int og) -> bool {
       const int u = og & 1;
       if (!mbar_wait(bar_of + 2 * g + u, (og >> 1) & 1, &fail)) return false;
       fence_after();
-      float v[TH];
-      const uint32_t oa = tbase + lane_off + Ly::T_O + (2 * g + u) * T + h * TH;
-      if constexpr (TH == 8) {
-        uint32_t rr[8];
-        tmem_ld8(oa, rr);
+      const uint32_t oa = tbase + lane_off + Ly::T_O + (2 * g + u) * 2 * T + h * TH;
+      // two 8-column pieces: O[0, T) (K_hi V_hi + K_lo V_hi) and O[T, 2T) (K_hi V_lo)
+#pragma unroll
+      for (int c8 = 0; c8 < TH; c8 += 8) {
+        uint32_t rr[8], rx[8];
+        tmem_ld8(oa + c8, rr);
+        if (p.split) tmem_ld8(oa + T + c8, rx);
         tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(rr[c]);
-      } else {
-        uint32_t rr[16];
-        tmem_ld16(oa, rr);
-        tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(rr[c]);
+        for (int c = 0; c < 8; ++c)
+          kahan(c8 + c, __uint_as_float(rr[c]) + (p.split ? __uint_as_float(rx[c]) : 0.f));
       }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_oe + 2 * g + u);
-#pragma unroll
-      for (int c = 0; c < TH; ++c) {
-        const float yv = v[c] - cmp[c];
-        const float tv = acc[c] + yv;
-        cmp[c] = (tv - acc[c]) - yv;
-        acc[c] = tv;
-      }
       return true;
     };
     bool ok = true;
@@ -469,21 +476,14 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
         uint32_t sh[16], sx[16];
         tmem_ld16(sa, sh);
         if (p.split) tmem_ld16(sa + Ly::T_X, sx);
-        float nb[16];
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const float4 v4 = snb[c4];
-          nb[4 * c4 + 0] = v4.x;
-          nb[4 * c4 + 1] = v4.y;
-          nb[4 * c4 + 2] = v4.z;
-          nb[4 * c4 + 3] = v4.w;
-        }
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
+          const float4 n4 = snb[c >> 2];      // broadcast load, 4 norms per LDS.128
+          const float nbc = (c & 3) == 0 ? n4.x : (c & 3) == 1 ? n4.y : (c & 3) == 2 ? n4.z : n4.w;
           float sab = __uint_as_float(sh[c]);
           if (p.split) sab += __uint_as_float(sx[c]);
-          const float u2 = fmaxf(fmaf(-2.f, sab, na + nb[c]), 0.f);
+          const float u2 = fmaxf(fmaf(-2.f, sab, na + nbc), 0.f);
           const float uu = sqrt_approx(u2);
           const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
           // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder
