@@ -181,6 +181,36 @@ GP_API int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
                       int precision, double* logml, double* logdet,
                       double* grad, double* logdet_stderr, gp_stats* stats);
 
+/* ---- K-hat V without any allocation ---------------------------------------
+ * For callers that cannot allocate device memory (a process whose memory is
+ * reserved by another framework's pool, a real-time loop where cudaMalloc /
+ * cudaFree and the synchronisation they imply are not allowed).  The paper
+ * has no counterpart: this is a deployment variant of gp_kmatmul with
+ * GP_FP32_PLAIN arithmetic.  It calls no cudaMalloc, cudaFree,
+ * cudaMallocHost or other allocating routine and needs no context: its
+ * scratch (column means, prepared features, row norms) is one fixed
+ * file-scope device array of about 4.4 MiB, which every GPU that loads the
+ * library holds until the process exits.
+ *  - X, V, out: as in gp_kmatmul (device; V and out t x N column-major;
+ *    out must not alias V).  stream: a cudaStream_t (NULL = default).
+ *  - Limits: N <= GP_NOALLOC_MAX_ROWS, d <= GP_NOALLOC_MAX_D,
+ *    round_up(N, 64) * round_up(d, 32) <= GP_NOALLOC_MAX_FEATURES,
+ *    1 <= t <= 512; larger sizes return GP_EINVAL before any work.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents:
+ *    calls that overlap on the GPU (other streams, other host threads) race
+ *    and must be serialised by the caller.
+ *  - Asynchronous on `stream`; errors: GP_EINVAL (sizes, pointers,
+ *    hyperparameters), GP_ECUDA (a launch failed). */
+#define GP_NOALLOC_MAX_ROWS 65536
+#define GP_NOALLOC_MAX_D 256
+#define GP_NOALLOC_MAX_FEATURES (1 << 20)
+GP_API int gp_kmatmul_noalloc(const float* X, int64_t N, int d,
+                              const gp_theta* theta, const float* V, int t,
+                              float* out, void* stream);
+
 /* ---- trained model and prediction (Eq. pred) ------------------------------
  * gp_model_fit keeps, on the device, the prepared features, a = K-hat^{-1} y
  * (mBCG to `tol`), the preconditioner factor and the hyperparameters.

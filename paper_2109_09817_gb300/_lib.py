@@ -18,6 +18,7 @@ EXPORTS = (
     "gp_create", "gp_destroy", "gp_set_stream", "gp_sync", "gp_last_error",
     "gp_launch_count", "gp_profile", "gp_profile_read", "gp_kmatmul", "gp_kcross_matmul", "gp_pivchol", "gp_mbcg",
     "gp_logml_and_grad", "gp_model_fit", "gp_model_free", "gp_predict",
+    "gp_kmatmul_noalloc",
 )
 
 
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(vp), st]),
         "gp_model_free": (None, [vp]),
         "gp_predict": (c_int, [vp, vp, vp, i64, vp, vp, c_int]),
+        "gp_kmatmul_noalloc": (c_int, [vp, i64, c_int, th, vp, c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
