@@ -70,6 +70,15 @@ enum {
   GP_BF16 = 4             /* tcgen05 kind::f16 (bf16), single-pass          */
 };
 
+/* preconditioner forms (P = L L^T + D, L from the rank-k pivoted Cholesky) */
+enum {
+  GP_PC_SIGMA = 0,  /* D = sigma^2 I: the form of Sec. 3.2                   */
+  GP_PC_RESID = 1   /* D = diag(K - L L^T) + sigma^2 I: the residual diagonal
+                       of the same factorisation is kept (reduces to the first
+                       form when K is close to rank k; stays well conditioned
+                       when K is close to diagonal)                          */
+};
+
 /* posterior variance modes of gp_predict */
 enum { GP_VAR_NONE = 0, GP_VAR_EXACT = 1 };
 
@@ -141,15 +150,19 @@ GP_API int gp_kcross_matmul(gp_ctx* ctx, const float* Xp, int64_t M, const float
  * is set to zero.  Stops early when the largest residual diagonal is
  * <= 1e-12 s.  L: N x k FP64 column-major (column j at L + j*N); columns
  * past the rank reached are zero.  piv: k int64 (past the rank: -1).
- * rank_out: HOST int.  Synchronises. */
+ * rank_out: HOST int.  resid_diag (nullable, N doubles, device): the
+ * residual diagonal diag(K - L L^T) after the last step, zero at the pivots.
+ * Synchronises. */
 GP_API int gp_pivchol(gp_ctx* ctx, const float* X, int64_t N, int d,
                const gp_theta* theta, int k, double* L, int64_t* piv,
-               int* rank_out);
+               int* rank_out, double* resid_diag);
 
 /* ---- mBCG (Sec. 3.2; CG of Sec. 3.1 with preconditioner P) ----------------
  * Solves K-hat Omega = B for t right-hand sides at once with preconditioned
- * CG, P = L L^T + sigma^2 I applied by the Woodbury identity (L from
- * gp_pivchol, rank k; k = 0 means P = sigma^2 I, i.e. plain CG).  Every
+ * CG, P = L L^T + D applied by the Woodbury identity (L from gp_pivchol,
+ * rank k; D = sigma^2 I, or diag(resid_diag) + sigma^2 I when resid_diag
+ * (device, N doubles, from gp_pivchol) is given; k = 0 and no resid_diag
+ * means P = sigma^2 I, i.e. plain CG).  Every
  * column shares each K-hat product.  Column c stops (is frozen) once
  * ||r_c|| / ||b_c|| < tol (Sec. 4 stop rule); the solve stops when all
  * columns stopped or after max_iter steps (then GP_ENOTCONV).
@@ -159,14 +172,17 @@ GP_API int gp_pivchol(gp_ctx* ctx, const float* X, int64_t N, int d,
  * Lanczos tridiagonal of column c follows from its first iters[c] entries.
  * iters, rel_resid: nullable HOST arrays of t.  Synchronises. */
 GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
-            const gp_theta* theta, const double* L, int k, const float* B,
+            const gp_theta* theta, const double* L, int k,
+            const double* resid_diag, const float* B,
             int t, double tol, int max_iter, int precision, float* Omega,
             double* alpha_hist, double* beta_hist, int* iters,
             double* rel_resid);
 
 /* ---- log marginal likelihood and gradient (Eq. ll; Sec. 3.2) -------------
- * One pass of the whole training path: rank-k pivoted Cholesky; probes
- * z_c = L e1_c + sigma e2_c (c < n_probes) with Rademacher signs from the
+ * One pass of the whole training path: rank-k pivoted Cholesky and the
+ * preconditioner P = L L^T + D of form `precond` (GP_PC_SIGMA or
+ * GP_PC_RESID); probes z_c = L e1_c + D^{1/2} e2_c (c < n_probes), so that
+ * Cov(z) = P, with Rademacher signs from the
  * SplitMix64 sequence seeded by `seed`; mBCG on [y | z_1..z_t]; Lanczos
  * quadrature of log|K-hat|; and the gradient
  *   dL/dtheta = 1/2 a^T dK a - 1/(2t) sum_c (K-hat^{-1} z_c)^T dK (P^{-1} z_c)
@@ -177,7 +193,7 @@ GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
  * Synchronises. */
 GP_API int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
                       const gp_theta* theta, const float* y, int n_probes,
-                      uint64_t seed, int k, double tol, int max_iter,
+                      uint64_t seed, int k, int precond, double tol, int max_iter,
                       int precision, double* logml, double* logdet,
                       double* grad, double* logdet_stderr, gp_stats* stats);
 
@@ -216,7 +232,7 @@ GP_API int gp_kmatmul_noalloc(const float* X, int64_t N, int d,
  * (mBCG to `tol`), the preconditioner factor and the hyperparameters.
  * X and y are copied; the caller may free them afterwards.  Synchronises. */
 GP_API int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
-                 const gp_theta* theta, const float* y, int k, double tol,
+                 const gp_theta* theta, const float* y, int k, int precond, double tol,
                  int max_iter, int precision, gp_model** out,
                  gp_stats* stats);
 GP_API void gp_model_free(gp_model* model);

@@ -20,6 +20,12 @@ Readings where the paper is silent (all listed in the design notes):
 * Pivot ties are broken by the lowest index; a pivot is taken out of the
   candidate set by zeroing its residual diagonal; the factorisation stops
   early when the largest residual diagonal is <= 1e-12 * s.
+* Preconditioner form.  Sec. 3.2 uses the pivoted Cholesky factor as
+  P = L L^T + sigma^2 I; Sec. 3.2 also notes that better preconditioners may
+  exist.  Besides that form the oracle provides the diagonal-corrected
+  P = L L^T + D, D = diag(K - L L^T) + sigma^2 I (the residual diagonal of
+  the same factorisation), which equals the first form when K is close to
+  rank k and stays well conditioned when K is close to diagonal.
 """
 from __future__ import annotations
 
@@ -38,6 +44,7 @@ __all__ = [
     "khat_matmul_rows", "kcross_matmul", "cholesky_solve", "exact_logdet",
     "log_marginal_likelihood", "pivoted_cholesky", "precond_solve",
     "precond_logdet", "splitmix64_signs", "probe_signs", "probe_vectors",
+    "residual_diagonal", "precond_diag",
     "mbcg", "lanczos_tridiagonal", "quadrature_log", "slq_logdet",
     "same_probe_logdet_target", "dkhat_dtheta", "exact_grad",
     "same_probe_grad", "predict", "true_relative_residual",
@@ -160,22 +167,43 @@ def pivoted_cholesky(X, lengthscale, s, k, stop_rel=1e-12):
     return L[:, :r], np.asarray(piv, dtype=np.int64), np.asarray(gaps)
 
 
-def precond_solve(L, sigma2, V):
-    """P^{-1} V with P = L L^T + sigma^2 I, by the Woodbury identity:
-    P^{-1} v = (v - L (sigma^2 I_k + L^T L)^{-1} L^T v) / sigma^2."""
+def residual_diagonal(X, lengthscale, s, L, piv):
+    """diag(K - L L^T) with the pivots' entries set to zero (their residual
+    is removed by the factorisation)."""
+    d = float(s) - np.sum(np.asarray(L, F64) ** 2, axis=1)
+    d[np.asarray(piv, dtype=np.int64)] = 0.0
+    return d
+
+
+def precond_diag(L, sigma2, resid=None):
+    """The diagonal D of P = L L^T + D: sigma^2 (form of Sec. 3.2) or
+    resid + sigma^2 (diagonal-corrected form)."""
+    N = L.shape[0]
+    if resid is None:
+        return np.full(N, float(sigma2))
+    return np.asarray(resid, F64) + sigma2
+
+
+def precond_solve(L, sigma2, V, resid=None):
+    """P^{-1} V with P = L L^T + D, by the Woodbury identity:
+    P^{-1} v = D^{-1} v - D^{-1} L (I_k + L^T D^{-1} L)^{-1} L^T D^{-1} v.
+    With D = sigma^2 I this is (v - L (sigma^2 I_k + L^T L)^{-1} L^T v)/sigma^2."""
     V = np.asarray(V, F64)
-    C = sigma2 * np.eye(L.shape[1]) + L.T @ L
-    W = np.linalg.solve(C, L.T @ V)
-    return (V - L @ W) / sigma2
+    Dinv = 1.0 / precond_diag(L, sigma2, resid)
+    DV = Dinv[:, None] * V if V.ndim == 2 else Dinv * V
+    C = np.eye(L.shape[1]) + L.T @ (Dinv[:, None] * L)
+    W = np.linalg.solve(C, L.T @ DV)
+    LW = L @ W
+    return DV - (Dinv[:, None] * LW if V.ndim == 2 else Dinv * LW)
 
 
-def precond_logdet(L, sigma2, N):
-    """log|P| = (N - k) log sigma^2 + log|sigma^2 I_k + L^T L|."""
-    k = L.shape[1]
-    C = sigma2 * np.eye(k) + L.T @ L
+def precond_logdet(L, sigma2, N, resid=None):
+    """log|P| = sum_a log D_a + log|I_k + L^T D^{-1} L|."""
+    D = precond_diag(L, sigma2, resid)
+    C = np.eye(L.shape[1]) + L.T @ (L / D[:, None])
     sign, ld = np.linalg.slogdet(C)
     assert sign > 0
-    return (N - k) * math.log(sigma2) + ld
+    return float(np.sum(np.log(D)) + ld)
 
 
 # ----------------------------------------------------------------------------
@@ -211,13 +239,13 @@ def probe_signs(seed, stream, n_rows, n_probes):
     return splitmix64_signs(seed, ctr)
 
 
-def probe_vectors(L, sigma2, seed, n_probes):
-    """z_c = L e1_c + sigma e2_c, e1 in {+-1}^k (stream 1), e2 in {+-1}^N
-    (stream 0), so that Cov(z) = P."""
+def probe_vectors(L, sigma2, seed, n_probes, resid=None):
+    """z_c = L e1_c + D^{1/2} e2_c, e1 in {+-1}^k (stream 1), e2 in {+-1}^N
+    (stream 0), so that Cov(z) = P = L L^T + D."""
     N, k = L.shape
     e2 = probe_signs(seed, 0, N, n_probes)
     e1 = probe_signs(seed, 1, k, n_probes)
-    return L @ e1 + math.sqrt(sigma2) * e2
+    return L @ e1 + np.sqrt(precond_diag(L, sigma2, resid))[:, None] * e2
 
 
 # ----------------------------------------------------------------------------
@@ -297,7 +325,7 @@ def quadrature_log(diag, off):
     return float(np.sum(Q[0, :] ** 2 * np.log(lam)))
 
 
-def slq_logdet(res, L, sigma2, N):
+def slq_logdet(res, L, sigma2, N, resid=None):
     """log|K-hat| ~ log|P| + (1/t) sum_c ||w_c||^2 e1^T log(T_c) e1 with
     ||w_c||^2 = z_c^T P^{-1} z_c = r0^T z0 (Sec. 3.2: mBCG estimates of
     the log marginal likelihood).  ``res`` is ``mbcg`` output on the probe
@@ -308,15 +336,15 @@ def slq_logdet(res, L, sigma2, N):
         dg, of = lanczos_tridiagonal(res["alpha"][c], res["beta"][c],
                                      int(res["iters"][c]))
         acc += res["rz0"][c] * quadrature_log(dg, of)
-    return precond_logdet(L, sigma2, N) + acc / t
+    return precond_logdet(L, sigma2, N, resid) + acc / t
 
 
-def same_probe_logdet_target(Khat, L, sigma2, Zp):
+def same_probe_logdet_target(Khat, L, sigma2, Zp, resid=None):
     """The value the stochastic estimate converges to for these probes:
     log|P| + (1/t) sum_c z_c^T P^{-1/2} log(A) P^{-1/2} z_c,
     A = P^{-1/2} K-hat P^{-1/2}, by dense eigendecompositions."""
     N = Khat.shape[0]
-    P = L @ L.T + sigma2 * np.eye(N)
+    P = L @ L.T + np.diag(precond_diag(L, sigma2, resid))
     lp, Qp = np.linalg.eigh(P)
     Pmh = (Qp / np.sqrt(lp)) @ Qp.T
     A = Pmh @ Khat @ Pmh

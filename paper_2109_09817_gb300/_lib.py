@@ -12,6 +12,7 @@ ERROR_NAMES = {0: "GP_OK", 1: "GP_EINVAL", 2: "GP_ENOMEM", 3: "GP_ENOTCONV",
                4: "GP_EBREAKDOWN", 5: "GP_ENONPD", 6: "GP_ETIMEOUT", 7: "GP_ECUDA"}
 GP_FP32_PLAIN, GP_FP32_SPLIT_TF32, GP_BF16_SPLIT, GP_TF32, GP_BF16 = range(5)
 GP_VAR_NONE, GP_VAR_EXACT = 0, 1
+GP_PC_SIGMA, GP_PC_RESID = 0, 1
 
 # Every symbol include/gp.h declares.
 EXPORTS = (
@@ -68,12 +69,12 @@ def load(path: str = LIB_PATH):
         "gp_profile_read": (c_int, [vp, ctypes.POINTER(i64), dp, dp, dp]),
         "gp_kmatmul": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, c_int]),
         "gp_kcross_matmul": (c_int, [vp, vp, i64, vp, i64, c_int, th, vp, c_int, vp, c_int]),
-        "gp_pivchol": (c_int, [vp, vp, i64, c_int, th, c_int, vp, vp, ip]),
-        "gp_mbcg": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, c_int, c_dbl, c_int,
+        "gp_pivchol": (c_int, [vp, vp, i64, c_int, th, c_int, vp, vp, ip, vp]),
+        "gp_mbcg": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, vp, c_int, c_dbl, c_int,
                             c_int, vp, vp, vp, ip, dp]),
         "gp_logml_and_grad": (c_int, [vp, vp, i64, c_int, th, vp, c_int, ctypes.c_uint64,
-                                      c_int, c_dbl, c_int, c_int, dp, dp, dp, dp, st]),
-        "gp_model_fit": (c_int, [vp, vp, i64, c_int, th, vp, c_int, c_dbl, c_int, c_int,
+                                      c_int, c_int, c_dbl, c_int, c_int, dp, dp, dp, dp, st]),
+        "gp_model_fit": (c_int, [vp, vp, i64, c_int, th, vp, c_int, c_int, c_dbl, c_int, c_int,
                                  ctypes.POINTER(vp), st]),
         "gp_model_free": (None, [vp]),
         "gp_predict": (c_int, [vp, vp, vp, i64, vp, vp, c_int]),

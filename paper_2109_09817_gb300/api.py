@@ -19,7 +19,7 @@ import torch
 from . import _lib
 from ._lib import (GP_BF16, GP_BF16_SPLIT, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
                    GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_OK, GP_ENOTCONV,
-                   GP_EBREAKDOWN, ERROR_NAMES)
+                   GP_EBREAKDOWN, GP_EINVAL, GP_PC_SIGMA, GP_PC_RESID, ERROR_NAMES)
 
 PRECISIONS = {"fp32": GP_FP32_PLAIN, "split_tf32": GP_FP32_SPLIT_TF32,
               "split_bf16": GP_BF16_SPLIT, "tf32": GP_TF32, "bf16": GP_BF16}
@@ -139,24 +139,30 @@ def gp_kcross_matmul(ctx: Context, Xp: torch.Tensor, X: torch.Tensor, theta: The
     return out
 
 
-def gp_pivchol(ctx: Context, X: torch.Tensor, theta: Theta, k: int):
-    """Rank-k pivoted Cholesky (FP64).  Returns (L (k, N) float64, piv (k,), rank)."""
+def gp_pivchol(ctx: Context, X: torch.Tensor, theta: Theta, k: int, want_resid: bool = False):
+    """Rank-k pivoted Cholesky (FP64).  Returns (L (k, N) float64, piv (k,),
+    rank), plus the residual diagonal (N,) float64 when ``want_resid``."""
     _dev(ctx, X, torch.float32, "X")
     N, d = X.shape
     L = torch.empty((max(k, 1), N), dtype=torch.float64, device=X.device)
     piv = torch.empty(max(k, 1), dtype=torch.int64, device=X.device)
+    res = torch.empty(N, dtype=torch.float64, device=X.device) if want_resid else None
     rank = ctypes.c_int(0)
     th, keep = theta.as_c()
     ctx.check(ctx.lib.gp_pivchol(ctx.h, _p(X), N, d, ctypes.byref(th), k, _p(L), _p(piv),
-                                 ctypes.byref(rank)))
+                                 ctypes.byref(rank), _p(res)))
+    if want_resid:
+        return L[:k], piv[:k], rank.value, res
     return L[:k], piv[:k], rank.value
 
 
 def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tensor],
             B: torch.Tensor, tol: float = 1e-6, max_iter: int = 1000,
-            precision: int = GP_FP32_PLAIN, allow_notconv: bool = True):
+            precision: int = GP_FP32_PLAIN, allow_notconv: bool = True,
+            resid: Optional[torch.Tensor] = None):
     """Batched PCG on K-hat Omega = B; returns dict(Omega, alpha, beta, iters,
-    relres, rc).  L: (k, N) float64 from gp_pivchol or None."""
+    relres, rc).  L: (k, N) float64 from gp_pivchol or None; resid: its
+    residual diagonal for the GP_PC_RESID form, or None for P = L L^T + sigma^2 I."""
     _dev(ctx, X, torch.float32, "X")
     N, d = X.shape
     B = _block(ctx, B, N, "B")
@@ -171,7 +177,9 @@ def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tenso
     rr = (ctypes.c_double * t)()
     th, keep = theta.as_c()
     allow = (GP_ENOTCONV,) if allow_notconv else ()
-    rc = ctx.check(ctx.lib.gp_mbcg(ctx.h, _p(X), N, d, ctypes.byref(th), _p(L), k, _p(B), t,
+    if resid is not None:
+        _dev(ctx, resid, torch.float64, "resid")
+    rc = ctx.check(ctx.lib.gp_mbcg(ctx.h, _p(X), N, d, ctypes.byref(th), _p(L), k, _p(resid), _p(B), t,
                                    tol, max_iter, precision, _p(Om), _p(ah), _p(bh), iters, rr),
                    allow=allow)
     return dict(Omega=Om, alpha=ah, beta=bh, iters=np.array(iters[:]),
@@ -181,7 +189,8 @@ def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tenso
 def gp_logml_and_grad(ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tensor,
                       n_probes: int = 15, seed: int = 0, k: int = 32, tol: float = 1e-6,
                       max_iter: int = 1000, precision: int = GP_FP32_PLAIN,
-                      want_grad: bool = True, allow_notconv: bool = False):
+                      want_grad: bool = True, allow_notconv: bool = False,
+                      precond: int = GP_PC_SIGMA):
     """Eq. (ll) and its gradient (natural parameters l_1..l_d, s, sigma^2)."""
     _dev(ctx, X, torch.float32, "X")
     _dev(ctx, y, torch.float32, "y")
@@ -194,7 +203,7 @@ def gp_logml_and_grad(ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tens
     th, keep = theta.as_c()
     allow = (GP_ENOTCONV,) if allow_notconv else ()
     rc = ctx.check(ctx.lib.gp_logml_and_grad(
-        ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), n_probes, ctypes.c_uint64(seed), k, tol,
+        ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), n_probes, ctypes.c_uint64(seed), k, precond, tol,
         max_iter, precision, ctypes.byref(logml), ctypes.byref(logdet),
         grad if want_grad else None, ctypes.byref(se), ctypes.byref(stats)), allow=allow)
     return dict(logml=logml.value, logdet=logdet.value, logdet_stderr=se.value,
@@ -206,7 +215,7 @@ class Model:
 
     def __init__(self, ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tensor,
                  k: int = 32, tol: float = 1e-6, max_iter: int = 1000,
-                 precision: int = GP_FP32_PLAIN):
+                 precision: int = GP_FP32_PLAIN, precond: int = GP_PC_SIGMA):
         _dev(ctx, X, torch.float32, "X")
         _dev(ctx, y, torch.float32, "y")
         self.ctx = ctx
@@ -215,7 +224,7 @@ class Model:
         h = ctypes.c_void_p()
         stats = _lib.GpStats()
         th, keep = theta.as_c()
-        ctx.check(ctx.lib.gp_model_fit(ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), k, tol,
+        ctx.check(ctx.lib.gp_model_fit(ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), k, precond, tol,
                                        max_iter, precision, ctypes.byref(h), ctypes.byref(stats)))
         self.h = h
         self.stats = stats.as_dict()
@@ -233,8 +242,8 @@ class Model:
 
 
 def gp_model_fit(ctx: Context, X, theta, y, k=32, tol=1e-6, max_iter=1000,
-                 precision=GP_FP32_PLAIN) -> Model:
-    return Model(ctx, X, theta, y, k, tol, max_iter, precision)
+                 precision=GP_FP32_PLAIN, precond=GP_PC_SIGMA) -> Model:
+    return Model(ctx, X, theta, y, k, tol, max_iter, precision, precond)
 
 
 def gp_predict(ctx: Context, model: Model, Xp: torch.Tensor, var_mode: int = GP_VAR_NONE):

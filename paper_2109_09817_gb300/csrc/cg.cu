@@ -79,11 +79,13 @@ __global__ void copy_kernel(const float* __restrict__ src, int64_t lds,
   }
 }
 
-// ---- preconditioner P^{-1} = (I - L (sigma2 I + L^T L)^{-1} L^T) / sigma2 --
-// G partials: part[b][j * t + c] = sum_{a in chunk b} L32[j][a] R[c][a]
+// ---- preconditioner P^{-1} = D^{-1/2} (I - L~ C^{-1} L~^T) D^{-1/2} --------
+// with L~ = D^{-1/2} L and C = I + L~^T L~ (FP64, inverse precomputed).
+// G partials: part[b][j * t + c] = sum_{a in chunk b} L~[j][a] dh[a] R[c][a]
 __global__ void ltr_partial_kernel(const float* __restrict__ L32, int64_t ldl,
                                    int k, const float* __restrict__ R, int64_t ldr,
                                    int t, int64_t n, const CgScal* __restrict__ sc,
+                                   const float* __restrict__ dh,
                                    double* __restrict__ part) {
   __shared__ float sL[64][65];
   __shared__ float sR[64][65];
@@ -103,7 +105,7 @@ __global__ void ltr_partial_kernel(const float* __restrict__ L32, int64_t ldl,
       const int64_t row = rb + rr;
       sL[jj][rr] = (jj < nj && row < r1) ? L32[(int64_t)(j0 + jj) * ldl + row] : 0.f;
       const bool act = jj < ncol && (!sc || sc[c0 + jj].active);
-      sR[jj][rr] = (act && row < r1) ? R[(int64_t)(c0 + jj) * ldr + row] : 0.f;
+      sR[jj][rr] = (act && row < r1) ? R[(int64_t)(c0 + jj) * ldr + row] * dh[row] : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -142,7 +144,7 @@ __global__ void g_reduce_kernel(const double* __restrict__ part, int nblk, int k
   G[idx] = s;
 }
 
-// w = C^{-1} G (C = sigma2 I + L^T L, inverse precomputed in FP64); wf k x t.
+// w = C^{-1} G (C = I + L~^T L~, inverse precomputed in FP64); wf k x t.
 __global__ void w_apply_kernel(const double* __restrict__ Cinv,
                                const double* __restrict__ G, int k, int t,
                                float* __restrict__ wf) {
@@ -154,11 +156,12 @@ __global__ void w_apply_kernel(const double* __restrict__ Cinv,
   wf[idx] = (float)s;
 }
 
-// Z_c = (R_c - L32 w_c) / sigma2 on 32-column chunks; rz partials.
+// Z_c = dh o (dh o R_c - L~ w_c) on 32-column chunks (dh = D^{-1/2};
+// without a preconditioner, dh = null and Z = R); rz partials.
 __global__ void z_apply_kernel(const float* __restrict__ L32, int64_t ldl, int k,
                                const float* __restrict__ wf, int t,
                                const float* __restrict__ R, float* __restrict__ Z,
-                               int64_t ld, int64_t n, float inv_s2,
+                               int64_t ld, int64_t n, const float* __restrict__ dh,
                                const CgScal* __restrict__ sc,
                                double* __restrict__ rzpart) {
   extern __shared__ float sw[];   // k x 32 chunk of w
@@ -193,7 +196,7 @@ __global__ void z_apply_kernel(const float* __restrict__ L32, int64_t ldl, int k
       if (!act[cc]) continue;
       const int64_t o = (int64_t)(c0 + cc) * ld + a;
       const float r = R[o];
-      const float z = (r - acc[cc]) * inv_s2;
+      const float z = dh ? dh[a] * fmaf(dh[a], r, -acc[cc]) : r;
       Z[o] = z;
       rz[cc] += (double)r * (double)z;
     }
@@ -349,8 +352,8 @@ __device__ __forceinline__ float splitmix_sign(uint64_t seed, uint64_t ctr) {
 }
 
 __global__ void probe_kernel(const double* __restrict__ L, int64_t n, int k,
-                             double sigma, uint64_t seed, int np,
-                             float* __restrict__ Z, int64_t ldz) {
+                             double sigma2, const double* __restrict__ resid,
+                             uint64_t seed, int np, float* __restrict__ Z, int64_t ldz) {
   extern __shared__ float se1[];   // k x np
   for (int idx = threadIdx.x; idx < k * np; idx += blockDim.x) {
     const int i = idx / np, c = idx % np;
@@ -360,8 +363,9 @@ __global__ void probe_kernel(const double* __restrict__ L, int64_t n, int k,
   __syncthreads();
   for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
        a += (int64_t)gridDim.x * blockDim.x) {
+    const double sd = sqrt((resid ? resid[a] : 0.0) + sigma2);   // D_a^{1/2}
     for (int c = 0; c < np; ++c) {
-      double z = sigma * (double)splitmix_sign(seed, ((uint64_t)c << 32) | (uint64_t)a);
+      double z = sd * (double)splitmix_sign(seed, ((uint64_t)c << 32) | (uint64_t)a);
       for (int i = 0; i < k; ++i) z += L[(int64_t)i * n + a] * (double)se1[i * np + c];
       Z[(int64_t)c * ldz + a] = (float)z;
     }
@@ -391,13 +395,13 @@ int dot_columns(gp_ctx* ctx, const float* A, const float* B, int64_t ld,
   return GP_OK;
 }
 
-int probe_vectors(gp_ctx* ctx, const double* L, int64_t n, int k, double sigma,
-                  uint64_t seed, int n_probes, float* Z, int64_t ldz) {
+int probe_vectors(gp_ctx* ctx, const double* L, int64_t n, int k, double sigma2,
+                  const double* resid, uint64_t seed, int n_probes, float* Z, int64_t ldz) {
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms));
   const size_t shm = sizeof(float) * (size_t)std::max(1, k * n_probes);
   if (shm > 48 * 1024)
     GP_CUDA(ctx, cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  probe_kernel<<<g, 256, shm, ctx->stream>>>(L, n, k, sigma, seed, n_probes, Z, ldz);
+  probe_kernel<<<g, 256, shm, ctx->stream>>>(L, n, k, sigma2, resid, seed, n_probes, Z, ldz);
   GP_LAUNCHED(ctx);
   return GP_OK;
 }
@@ -406,7 +410,6 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
                               const float* R, float* Z, int64_t ld, int t,
                               const CgScal* sc, double* rzpart) {
   const int k = pc ? pc->k : 0;
-  const double sigma2 = pc ? pc->sigma2 : 1.0;
   float* wf = nullptr;
   if (k > 0) {
     const int nb = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 256)));
@@ -415,7 +418,7 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
     double* G = part + (size_t)nb * k * t;
     if (!part || !wf) return set_err(ctx, GP_ENOMEM, "workspace (precond)");
     dim3 grid(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 64));
-    ltr_partial_kernel<<<grid, 256, 0, ctx->stream>>>(pc->L32, pc->ld32, k, R, ld, t, n, sc, part);
+    ltr_partial_kernel<<<grid, 256, 0, ctx->stream>>>(pc->L32, pc->ld32, k, R, ld, t, n, sc, pc->dh, part);
     GP_LAUNCHED(ctx);
     const unsigned g2 = (unsigned)ceil_div((int64_t)k * t, 128);
     g_reduce_kernel<<<g2, 128, 0, ctx->stream>>>(part, nb, k, t, sc, G);
@@ -428,7 +431,7 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
     GP_CUDA(ctx, cudaFuncSetAttribute(z_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   dim3 grid(kRedBlocks, (unsigned)ceil_div(t, 32));
   z_apply_kernel<<<grid, 256, shm, ctx->stream>>>(pc ? pc->L32 : nullptr, pc ? pc->ld32 : 0, k, wf, t,
-                                                  R, Z, ld, n, (float)(1.0 / sigma2), sc, rzpart);
+                                                  R, Z, ld, n, pc ? pc->dh : nullptr, sc, rzpart);
   GP_LAUNCHED(ctx);
   return GP_OK;
 }

@@ -28,6 +28,7 @@ struct gp_model {
   int k = 0;
   float* L32 = nullptr;
   double* cfac = nullptr;
+  float* dh = nullptr;         // D^{-1/2}, n_pad
   double pc_logdet = 0.0;
 };
 
@@ -256,17 +257,19 @@ int gp_kcross_matmul(gp_ctx* ctx, const float* Xp, int64_t M, const float* X,
 
 int gp_pivchol(gp_ctx* ctx, const float* X, int64_t N, int d,
                const gp_theta* theta, int k, double* L, int64_t* piv,
-               int* rank_out) {
+               int* rank_out, double* resid_diag) {
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (k < 0 || k > N || (k > 0 && (!L || !piv)) || !rank_out)
     return set_err(ctx, GP_EINVAL, "gp_pivchol: bad k/L/piv/rank_out");
   *rank_out = 0;
   if (k == 0) return GP_OK;
-  return pivchol_run(ctx, X, N, d, theta->lengthscale, theta->outputscale, k, L, piv, rank_out);
+  return pivchol_run(ctx, X, N, d, theta->lengthscale, theta->outputscale, k, L, piv, rank_out,
+                     resid_diag);
 }
 
 int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
-            const gp_theta* theta, const double* L, int k, const float* B,
+            const gp_theta* theta, const double* L, int k,
+            const double* resid_diag, const float* B,
             int t, double tol, int max_iter, int precision, float* Omega,
             double* alpha_hist, double* beta_hist, int* iters,
             double* rel_resid) {
@@ -277,7 +280,7 @@ int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
   Prep p;
   GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
   Precond pc;
-  GP_TRY(precond_setup(ctx, L, N, k, k, theta->sigma2, &pc));
+  GP_TRY(precond_setup(ctx, L, N, k, k, theta->sigma2, resid_diag, &pc));
   double* ah = alpha_hist ? alpha_hist : ws<double>(ctx, WS_CG_AH, (size_t)max_iter * t);
   double* bh = beta_hist ? beta_hist : ws<double>(ctx, WS_CG_BH, (size_t)max_iter * t);
   int* iters_dev = static_cast<int*>(ws_get(ctx, WS_GR_ACC, sizeof(int) * t + sizeof(double) * t + 64));
@@ -319,12 +322,13 @@ int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
 
 int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
                       const gp_theta* theta, const float* y, int n_probes,
-                      uint64_t seed, int k, double tol, int max_iter,
+                      uint64_t seed, int k, int precond, double tol, int max_iter,
                       int precision, double* logml, double* logdet,
                       double* grad, double* logdet_stderr, gp_stats* stats) {
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!y || n_probes < 1 || n_probes > 255 || k < 0 || k > N || max_iter < 1 ||
-      !(tol >= 0.0) || !logml || !logdet || !valid_precision(precision))
+      !(tol >= 0.0) || !logml || !logdet || !valid_precision(precision) ||
+      (precond != GP_PC_SIGMA && precond != GP_PC_RESID))
     return set_err(ctx, GP_EINVAL, "gp_logml_and_grad: bad arguments");
   const double s = theta->outputscale, sig2 = theta->sigma2;
   Prep p;
@@ -336,9 +340,14 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
   int64_t* piv = static_cast<int64_t*>(ws_get(ctx, WS_PC_PIV, sizeof(int64_t) * std::max(k, 1)));
   if (!L || !piv) return set_err(ctx, GP_ENOMEM, "workspace (factor)");
   int rank = 0;
-  if (k > 0) GP_TRY(pivchol_run(ctx, X, N, d, theta->lengthscale, s, k, L, piv, &rank));
+  double* resid = nullptr;
+  if (k > 0 && precond == GP_PC_RESID) {
+    resid = ws<double>(ctx, WS_PC_RES, (size_t)N);
+    if (!resid) return set_err(ctx, GP_ENOMEM, "workspace (residual diagonal)");
+  }
+  if (k > 0) GP_TRY(pivchol_run(ctx, X, N, d, theta->lengthscale, s, k, L, piv, &rank, resid));
   Precond pc;
-  GP_TRY(precond_setup(ctx, L, N, k, rank, sig2, &pc));
+  GP_TRY(precond_setup(ctx, L, N, k, rank, sig2, resid, &pc));
   // 2. right-hand sides [y | z_1..z_t]
   float* B = ws<float>(ctx, WS_CG_B, (size_t)ld * T1);
   float* U = ws<float>(ctx, WS_CG_U, (size_t)ld * T1);
@@ -359,7 +368,7 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
   GP_CUDA(ctx, cudaMemsetAsync(Z0, 0, sizeof(float) * ld * T1, ctx->stream));
   GP_CUDA(ctx, cudaMemsetAsync(rec, 0, 64 * 1024, ctx->stream));
   GP_TRY(copy_vectors(ctx, y, N, B, ld, N, 1, 1.f));
-  GP_TRY(probe_vectors(ctx, L, N, rank, std::sqrt(sig2), seed, n_probes, B + ld, ld));
+  GP_TRY(probe_vectors(ctx, L, N, rank, sig2, resid, seed, n_probes, B + ld, ld));
   // 3. mBCG
   CgArgs a;
   a.prep = &p;
@@ -453,10 +462,11 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
 }
 
 int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
-                 const gp_theta* theta, const float* y, int k, double tol,
+                 const gp_theta* theta, const float* y, int k, int precond, double tol,
                  int max_iter, int precision, gp_model** out, gp_stats* stats) {
   GP_TRY(check_common(ctx, X, N, d, theta));
-  if (!y || !out || k < 0 || k > N || max_iter < 1 || !valid_precision(precision))
+  if (!y || !out || k < 0 || k > N || max_iter < 1 || !valid_precision(precision) ||
+      (precond != GP_PC_SIGMA && precond != GP_PC_RESID))
     return set_err(ctx, GP_EINVAL, "gp_model_fit: bad arguments");
   *out = nullptr;
   Prep p;
@@ -511,19 +521,27 @@ int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
   mp.xb_lo = m->xb_lo;
   // preconditioner
   int rank = 0;
+  double* resid = nullptr;
   if (k > 0) {
     if (cudaMalloc(&m->L, sizeof(double) * (size_t)N * k) != cudaSuccess)
       return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
     int64_t* piv = static_cast<int64_t*>(ws_get(ctx, WS_PC_PIV, sizeof(int64_t) * k));
     if (!piv) return fail(set_err(ctx, GP_ENOMEM, "workspace"));
-    int rc = pivchol_run(ctx, X, N, d, theta->lengthscale, m->s, k, m->L, piv, &rank);
+    if (precond == GP_PC_RESID) {
+      resid = ws<double>(ctx, WS_PC_RES, (size_t)N);
+      if (!resid) return fail(set_err(ctx, GP_ENOMEM, "workspace"));
+    }
+    int rc = pivchol_run(ctx, X, N, d, theta->lengthscale, m->s, k, m->L, piv, &rank, resid);
     if (rc != GP_OK) return fail(rc);
   }
   Precond pc;
   {
-    int rc = precond_setup(ctx, m->L, N, k, rank, m->sigma2, &pc);
+    int rc = precond_setup(ctx, m->L, N, k, rank, m->sigma2, resid, &pc);
     if (rc != GP_OK) return fail(rc);
   }
+  if (cudaMalloc(&m->dh, sizeof(float) * pc.ld32) != cudaSuccess)
+    return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
+  GP_CUDA(ctx, cudaMemcpyAsync(m->dh, pc.dh, sizeof(float) * pc.ld32, cudaMemcpyDeviceToDevice, st));
   m->k = rank;
   m->pc_logdet = pc.logdet;
   if (rank > 0) {
@@ -589,7 +607,7 @@ void gp_model_free(gp_model* m) {
   cudaDeviceSynchronize();
   for (void* q : {(void*)m->mu, (void*)m->xt, (void*)m->norm, (void*)m->xt_hi,
                   (void*)m->xt_lo, (void*)m->xb_hi, (void*)m->xb_lo, (void*)m->alpha,
-                  (void*)m->L, (void*)m->L32, (void*)m->cfac})
+                  (void*)m->L, (void*)m->L32, (void*)m->cfac, (void*)m->dh})
     if (q) cudaFree(q);
   delete m;
 }
@@ -624,6 +642,7 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, const float* Xp, int64_t M,
   pc.ld32 = m->n_pad;
   pc.cfac = m->cfac;
   pc.cinv = m->cfac ? m->cfac + (size_t)m->k * m->k : nullptr;
+  pc.dh = m->dh;
   pc.logdet = m->pc_logdet;
   pc.sigma2 = m->sigma2;
   const int CH = 64;

@@ -43,7 +43,7 @@ enum WsSlot {
   WS_PC_L, WS_PC_L32, WS_PC_D, WS_PC_PIV, WS_PC_STATE, WS_PC_GRAM, WS_PC_CF,
   WS_LZ_SCR, WS_LZ_OUT,
   WS_GR_U, WS_GR_W, WS_GR_ACC,
-  WS_PR_K, WS_PR_O, WS_STATUS,
+  WS_PR_K, WS_PR_O, WS_STATUS, WS_PC_DG, WS_PC_DH, WS_PC_RES,
   WS_COUNT
 };
 
@@ -150,22 +150,25 @@ int kmv_init_out(gp_ctx* ctx, const float* V, int64_t ldv, int t, int64_t n,
                  float* out, int64_t ldo, float sigma2);
 
 // ---- pivoted Cholesky (FP64) -------------------------------------------------
+// P = L L^T + D, D = sigma2 I or diag(resid) + sigma2 I
 struct Precond {
   int k = 0;               // rank reached
   int64_t n = 0;
   const double* L = nullptr;     // n x k_alloc FP64 column-major (ld n)
-  const float* L32 = nullptr;    // FP32 copy, ld n_pad
+  const double* resid = nullptr; // residual diagonal (device, nullable)
+  const float* L32 = nullptr;    // L~ = D^{-1/2} L in FP32, ld n_pad
+  const float* dh = nullptr;     // D^{-1/2}, n_pad floats (0 on padding)
   int64_t ld32 = 0;
-  const double* cfac = nullptr;  // k x k lower Cholesky of sigma2 I + L^T L
-  const double* cinv = nullptr;  // (sigma2 I + L^T L)^{-1}, k x k, FP64
+  const double* cfac = nullptr;  // k x k lower Cholesky of I + L~^T L~
+  const double* cinv = nullptr;  // (I + L~^T L~)^{-1}, k x k, FP64
   double logdet = 0.0;           // log|P|
   double sigma2 = 0.0;
 };
 int pivchol_run(gp_ctx* ctx, const float* X, int64_t n, int d,
                 const double* lengthscale_host, double s, int k, double* L,
-                int64_t* piv, int* rank_out);
+                int64_t* piv, int* rank_out, double* resid_out);
 int precond_setup(gp_ctx* ctx, const double* L, int64_t n, int k_alloc,
-                  int rank, double sigma2, Precond* out);
+                  int rank, double sigma2, const double* resid, Precond* out);
 
 // ---- mBCG --------------------------------------------------------------------
 struct CgResult {
@@ -216,8 +219,8 @@ int grad_tiles(gp_ctx* ctx, const Prep& p, const float* U, const float* W,
 // out[c] = sum_a A[c*ld + a] * B[c*ld + a] in FP64, c < t (device doubles)
 int dot_columns(gp_ctx* ctx, const float* A, const float* B, int64_t ld,
                 int64_t n, int t, double* out);
-int probe_vectors(gp_ctx* ctx, const double* L, int64_t n, int k, double sigma,
-                  uint64_t seed, int n_probes, float* Z, int64_t ldz);
+int probe_vectors(gp_ctx* ctx, const double* L, int64_t n, int k, double sigma2,
+                  const double* resid, uint64_t seed, int n_probes, float* Z, int64_t ldz);
 int copy_vectors(gp_ctx* ctx, const float* src, int64_t lds, float* dst,
                  int64_t ldd, int64_t n, int t, float scale);
 

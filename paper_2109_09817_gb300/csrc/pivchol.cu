@@ -6,8 +6,12 @@
 // d = diag(K - L L^T) (lowest index on ties), form the kernel column
 // K(X, x_p) in FP64 by direct differences, subtract L_{:,<j} L_{p,<j}^T,
 // divide by sqrt(d_p), update d -= l_j^2 and take p out (d_p = 0).
-// Stops early when max d <= 1e-12 s.  P = L L^T + sigma^2 I is applied by
-// the Woodbury identity with the k x k factor of sigma^2 I + L^T L (FP64).
+// Stops early when max d <= 1e-12 s.  The preconditioner is P = L L^T + D
+// with D = sigma^2 I (the form of Sec. 3.2) or D = diag(K - L L^T) + sigma^2 I
+// (diagonal-corrected: the residual diagonal d of the same factorisation).
+// P is applied by the Woodbury identity with L~ = D^{-1/2} L and the k x k
+// FP64 matrix C = I + L~^T L~:  P^{-1} = D^{-1/2} (I - L~ C^{-1} L~^T) D^{-1/2},
+// log|P| = sum_a log D_a + log|C|.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -149,7 +153,11 @@ __global__ void pc_column_kernel(const float* __restrict__ X, int64_t n, int d,
     for (int i = 0; i < j; ++i) col -= L[(int64_t)i * n + a] * lp[i];
     const double l = col * inv_sq;
     L[(int64_t)j * n + a] = l;
-    dres[a] = (a == p) ? 0.0 : dres[a] - l * l;
+    // the residual diagonal of a PSD Schur complement is >= 0 and exactly 0
+    // at a pivot: a pivot (and a row whose residual has reached 0) stays 0,
+    // rounding below 0 is clamped
+    const double dr = dres[a];
+    dres[a] = (a == p || dr == 0.0) ? 0.0 : fmax(dr - l * l, 0.0);
   }
 }
 
@@ -169,7 +177,8 @@ __device__ __forceinline__ void unrank_pair(int pidx, int& i, int& jj) {
 }
 
 __global__ void pc_gram_partial(const double* __restrict__ L, int64_t n, int k,
-                                int64_t rows_per_blk, double* __restrict__ part) {
+                                int64_t rows_per_blk, const double* __restrict__ Dg,
+                                double* __restrict__ part) {
   extern __shared__ double sl[];   // 32 rows x k
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
   const int64_t r1 = min(n, r0 + rows_per_blk);
@@ -189,7 +198,7 @@ __global__ void pc_gram_partial(const double* __restrict__ L, int64_t n, int k,
     for (int idx = threadIdx.x; idx < 32 * k; idx += blockDim.x) {
       const int rr = idx % 32, c = idx / 32;
       const int64_t row = rb + rr;
-      sl[rr * k + c] = row < r1 ? L[(int64_t)c * n + row] : 0.0;
+      sl[rr * k + c] = row < r1 ? L[(int64_t)c * n + row] / sqrt(Dg[row]) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -206,9 +215,9 @@ __global__ void pc_gram_partial(const double* __restrict__ L, int64_t n, int k,
   }
 }
 
-// C = sigma2 I + G; in-place lower Cholesky (one block); logdet of C.
+// C = I + G; in-place lower Cholesky (one block); logdet of C.
 __global__ void pc_small_chol(const double* __restrict__ part, int nparts, int k,
-                              double sigma2, double* __restrict__ C,
+                              double diag_add, double* __restrict__ C,
                               double* __restrict__ logdet_out, int* bad) {
   const int npairs = k * (k + 1) / 2;
   for (int pidx = threadIdx.x; pidx < npairs; pidx += blockDim.x) {
@@ -216,7 +225,7 @@ __global__ void pc_small_chol(const double* __restrict__ part, int nparts, int k
     unrank_pair(pidx, i, jj);
     double g = 0.0;
     for (int b = 0; b < nparts; ++b) g += part[(int64_t)b * npairs + pidx];
-    if (i == jj) g += sigma2;
+    if (i == jj) g += diag_add;
     C[i * k + jj] = g;
     C[jj * k + i] = (i == jj) ? g : 0.0;   // upper part cleared below
   }
@@ -266,13 +275,46 @@ __global__ void pc_small_inverse(const double* __restrict__ F, int k,
   }
 }
 
+// D_a = (resid_a or 0) + sigma2 (FP64), dh_a = D_a^{-1/2} (FP32, 0 on padding)
+__global__ void pc_diag_kernel(const double* __restrict__ resid, double sigma2, int64_t n,
+                               int64_t ld32, double* __restrict__ Dg, float* __restrict__ dh) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < ld32;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    if (a < n) {
+      const double D = (resid ? resid[a] : 0.0) + sigma2;
+      Dg[a] = D;
+      dh[a] = (float)(1.0 / sqrt(D));
+    } else {
+      dh[a] = 0.f;
+    }
+  }
+}
+
+// sum_a log D_a (FP64), fixed-order two-stage
+__global__ void pc_logd_partial(const double* __restrict__ Dg, int64_t n, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x)
+    acc += log(Dg[a]);
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// L~ = D^{-1/2} L in FP32, k_used x ld32 (zero on padding)
 __global__ void to_f32_kernel(const double* __restrict__ L, int64_t n, int k,
-                              float* __restrict__ L32, int64_t ld32) {
+                              const double* __restrict__ Dg, float* __restrict__ L32,
+                              int64_t ld32) {
   const int64_t total = (int64_t)k * ld32;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = i / ld32, a = i % ld32;
-    L32[i] = a < n ? (float)L[c * n + a] : 0.f;
+    L32[i] = a < n ? (float)(L[c * n + a] / sqrt(Dg[a])) : 0.f;
   }
 }
 
@@ -280,7 +322,7 @@ __global__ void to_f32_kernel(const double* __restrict__ L, int64_t n, int k,
 
 int pivchol_run(gp_ctx* ctx, const float* X, int64_t n, int d,
                 const double* lengthscale_host, double s, int k, double* L,
-                int64_t* piv, int* rank_out) {
+                int64_t* piv, int* rank_out, double* resid_out) {
   double* dres = ws<double>(ctx, WS_PC_D, (size_t)n);
   PcState* st = static_cast<PcState*>(ws_get(ctx, WS_PC_STATE, sizeof(PcState) + 64));
   double* pv = ws<double>(ctx, WS_PC_GRAM, 2 * kArgBlocks);
@@ -315,58 +357,74 @@ int pivchol_run(gp_ctx* ctx, const float* X, int64_t n, int d,
   GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *rank_out = hr[0];
   if (hr[1]) return set_err(ctx, GP_ENONPD, "pivoted Cholesky: non-finite residual diagonal at step %d", hr[0]);
+  if (resid_out)
+    GP_CUDA(ctx, cudaMemcpyAsync(resid_out, dres, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
   return GP_OK;
 }
 
 int precond_setup(gp_ctx* ctx, const double* L, int64_t n, int k_alloc,
-                  int rank, double sigma2, Precond* out) {
+                  int rank, double sigma2, const double* resid, Precond* out) {
   Precond pc;
   pc.n = n;
   pc.k = rank;
   pc.L = L;
   pc.sigma2 = sigma2;
+  pc.resid = resid;
   pc.ld32 = round_up(std::max<int64_t>(n, 1), kRowPad);
   (void)k_alloc;
-  if (rank == 0) {
-    pc.logdet = (double)n * std::log(sigma2);
-    *out = pc;
-    return GP_OK;
-  }
-  float* L32 = ws<float>(ctx, WS_PC_L32, (size_t)rank * pc.ld32);
-  double* cf = ws<double>(ctx, WS_PC_CF, (size_t)2 * rank * rank + 8);
-  const int npairs = rank * (rank + 1) / 2;
-  const int nblk = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 4096)), 2 * ctx->num_sms);
-  const int64_t rows_per_blk = ceil_div(n, nblk);
-  double* part = ws<double>(ctx, WS_PC_GRAM, (size_t)nblk * npairs + 2 * kArgBlocks);
-  if (!L32 || !cf || !part) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner)");
-  const unsigned eg = (unsigned)std::min<int64_t>(ceil_div((int64_t)rank * pc.ld32, 256), 16LL * ctx->num_sms);
-  to_f32_kernel<<<eg, 256, 0, ctx->stream>>>(L, n, rank, L32, pc.ld32);
+  double* Dg = ws<double>(ctx, WS_PC_DG, (size_t)pc.ld32 + 512);
+  float* dh = ws<float>(ctx, WS_PC_DH, (size_t)pc.ld32);
+  if (!Dg || !dh) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner diagonal)");
+  double* lpart = Dg + pc.ld32;   // 256 partial sums of log D
+  const unsigned eg0 = (unsigned)std::min<int64_t>(ceil_div(pc.ld32, 256), 16LL * ctx->num_sms);
+  pc_diag_kernel<<<eg0, 256, 0, ctx->stream>>>(resid, sigma2, n, pc.ld32, Dg, dh);
   GP_LAUNCHED(ctx);
-  const size_t shm = sizeof(double) * 32 * rank;
-  if (shm > 48 * 1024) {
-    GP_CUDA(ctx, cudaFuncSetAttribute(pc_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  }
-  dim3 ggrid(nblk, (unsigned)ceil_div(npairs, 8 * 256));
-  pc_gram_partial<<<ggrid, 256, shm, ctx->stream>>>(L, n, rank, rows_per_blk, part);
+  pc_logd_partial<<<256, 256, 0, ctx->stream>>>(Dg, n, lpart);
   GP_LAUNCHED(ctx);
+  pc.dh = dh;
+  double* cf = ws<double>(ctx, WS_PC_CF, (size_t)2 * std::max(rank, 1) * std::max(rank, 1) + 8);
+  if (!cf) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner)");
   double* cinv = cf + (size_t)rank * rank;
   double* ld_dev = cinv + (size_t)rank * rank;
   int* bad_dev = reinterpret_cast<int*>(ld_dev + 1);
-  GP_CUDA(ctx, cudaMemsetAsync(bad_dev, 0, sizeof(int), ctx->stream));
-  pc_small_chol<<<1, 256, 0, ctx->stream>>>(part, nblk, rank, sigma2, cf, ld_dev, bad_dev);
-  GP_LAUNCHED(ctx);
-  pc_small_inverse<<<1, 128, 0, ctx->stream>>>(cf, rank, cinv);
-  GP_LAUNCHED(ctx);
-  double* hb = static_cast<double*>(pinned_get(ctx, 2 * sizeof(double)));
+  GP_CUDA(ctx, cudaMemsetAsync(ld_dev, 0, 2 * sizeof(double), ctx->stream));
+  if (rank > 0) {
+    float* L32 = ws<float>(ctx, WS_PC_L32, (size_t)rank * pc.ld32);
+    const int npairs = rank * (rank + 1) / 2;
+    const int nblk = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 4096)), 2 * ctx->num_sms);
+    const int64_t rows_per_blk = ceil_div(n, nblk);
+    double* part = ws<double>(ctx, WS_PC_GRAM, (size_t)nblk * npairs + 2 * kArgBlocks);
+    if (!L32 || !part) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner)");
+    const unsigned eg = (unsigned)std::min<int64_t>(ceil_div((int64_t)rank * pc.ld32, 256), 16LL * ctx->num_sms);
+    to_f32_kernel<<<eg, 256, 0, ctx->stream>>>(L, n, rank, Dg, L32, pc.ld32);
+    GP_LAUNCHED(ctx);
+    const size_t shm = sizeof(double) * 32 * rank;
+    if (shm > 48 * 1024) {
+      GP_CUDA(ctx, cudaFuncSetAttribute(pc_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    }
+    dim3 ggrid(nblk, (unsigned)ceil_div(npairs, 8 * 256));
+    pc_gram_partial<<<ggrid, 256, shm, ctx->stream>>>(L, n, rank, rows_per_blk, Dg, part);
+    GP_LAUNCHED(ctx);
+    pc_small_chol<<<1, 256, 0, ctx->stream>>>(part, nblk, rank, 1.0, cf, ld_dev, bad_dev);
+    GP_LAUNCHED(ctx);
+    pc_small_inverse<<<1, 128, 0, ctx->stream>>>(cf, rank, cinv);
+    GP_LAUNCHED(ctx);
+    pc.L32 = L32;
+    pc.cfac = cf;
+    pc.cinv = cinv;
+  }
+  double* hb = static_cast<double*>(pinned_get(ctx, 260 * sizeof(double)));
+  if (!hb) return set_err(ctx, GP_ENOMEM, "pinned staging");
   GP_CUDA(ctx, cudaMemcpyAsync(hb, ld_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaMemcpyAsync(hb + 2, lpart, 256 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   int bad = 0;
   std::memcpy(&bad, hb + 1, sizeof(int));
-  if (bad) return set_err(ctx, GP_ENONPD, "sigma^2 I + L^T L is not positive definite");
-  pc.logdet = (double)(n - rank) * std::log(sigma2) + hb[0];
-  pc.L32 = L32;
-  pc.cfac = cf;
-  pc.cinv = cinv;
+  if (bad) return set_err(ctx, GP_ENONPD, "I + L~^T L~ is not positive definite");
+  double sumlogd = 0.0;
+  for (int i = 0; i < 256; ++i) sumlogd += hb[2 + i];
+  pc.logdet = sumlogd + hb[0];
   *out = pc;
   return GP_OK;
 }
