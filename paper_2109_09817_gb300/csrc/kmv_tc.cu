@@ -11,11 +11,16 @@
 //   MMA2  O_J = K_hi V_hi + K_hi V_lo + K_lo V_hi    (A operand from TMEM)
 //   epi   O_J drained from TMEM and added into per-thread registers with a
 //         compensated (Kahan) sum; flushed once per CTA with atomics.
-// S/K and O are double-buffered in TMEM so that the MMAs of one tile overlap
-// the epilogue of the next.  Warp roles: 0 TMA producer, 1 MMA issuer,
-// 2 TMEM allocator, 4..11 epilogue.  Every mbarrier wait is bounded: on a
-// timeout the kernel records GP_ETIMEOUT in a status word and all roles
-// leave their loops.
+// The tensor pipe loses roughly 500 cycles whenever it drains, so MMA1 runs
+// NSB tiles ahead of MMA2: S/K lives in NSB TMEM buffers (3 when the O
+// accumulators leave room, else 2), and MMA1 and MMA2 are issued by two
+// threads so that a wait in one does not starve the pipe.  X~_J tiles and
+// V_J tiles travel in separate TMA rings, so an X~_J slot is recycled as soon
+// as its MMA1 has run.  Warp roles: 0 TMA producer, 1 MMA1 issuer, 2 TMEM
+// allocator, 3 MMA2 issuer, 4..19 epilogue in two groups of 8 (group g takes
+// tiles j with j % 2 == g).
+// Every mbarrier wait is bounded: on a timeout the kernel records
+// GP_ETIMEOUT in a status word and all roles leave their loops.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -119,6 +124,27 @@ __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, 
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// The same with compile-time byte/16 offsets added to the SMEM descriptors
+// (and to the TMEM A address) inside the asm, so that the offsets stay
+// immediates instead of registers held across the tile loop.
+template <uint32_t AO, uint32_t BO>
+__device__ __forceinline__ void mma_ss_imm(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n add.s64 da, %1, %5;\n add.s64 db, %2, %6;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc), "n"(AO), "n"(BO)
+      : "memory");
+}
+template <uint32_t AO, uint32_t BO>
+__device__ __forceinline__ void mma_ts_imm(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b32 ta;\n .reg .b64 db;\n add.u32 ta, %1, %5;\n add.s64 db, %2, %6;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [ta], db, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc), "n"(AO), "n"(BO)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
@@ -184,9 +210,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float sqrt_approx(float x) {
+__device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -194,31 +220,38 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 template <int DP, int T>
 struct TcLayout {
   static constexpr int KB = DP / 32;                   // 128-byte K boxes of X~
-  static constexpr int STAGES = DP <= 32 ? 4 : 3;
+  static constexpr int NSB = T <= 16 ? 3 : 2;          // S/K buffers in TMEM
+  static constexpr int XS = DP <= 32 ? 4 : 3;          // X~_J ring slots
+  static constexpr int VS = T <= 16 ? NSB + 2 : NSB + 1;  // V_J ring slots (>= NSB)
   static constexpr int A_BOX = BM * 128;               // bytes per K box, A
   static constexpr int XJ_BOX = BN * 128;              // bytes per K box, X~_J
   static constexpr int V_BOX = T * 128;                // bytes per K box of V_J
   static constexpr int A_HI = 0;
   static constexpr int A_LO = A_HI + KB * A_BOX;
-  static constexpr int ST0 = A_LO + KB * A_BOX;
-  // per 128-byte K box kb of X~_J: [hi rows 0..63][lo rows 0..63], so that
-  // hi and lo stack into one N = 128 B operand; likewise V_J: [hi T rows][lo T rows]
-  static constexpr int S_X = 0;                        // + kb * 2 * XJ_BOX (+ XJ_BOX for lo)
-  static constexpr int S_V = S_X + KB * 2 * XJ_BOX;    // + vb * 2 * V_BOX (+ V_BOX for lo)
-  static constexpr int S_NRM = S_V + 2 * 2 * V_BOX;
-  static constexpr int STAGE_BYTES = (S_NRM + 256 + 1023) / 1024 * 1024;
-  static constexpr int BAR = ST0 + STAGES * STAGE_BYTES;
-  static constexpr int NBAR = 1 + 2 * STAGES + 4 + 8 + 1;
+  // X~_J slot: per 128-byte K box kb: [hi rows 0..63][lo rows 0..63], so that
+  // hi and lo stack into one N = 128 B operand
+  static constexpr int X_SLOT = KB * 2 * XJ_BOX;
+  static constexpr int X0 = A_LO + KB * A_BOX;
+  // V_J slot: per 32-column box vb: [hi T rows][lo T rows], then the 64
+  // column norms
+  static constexpr int V_NRM = 2 * 2 * V_BOX;
+  static constexpr int V_SLOT = (V_NRM + 256 + 1023) / 1024 * 1024;
+  static constexpr int V0 = X0 + XS * X_SLOT;
+  static constexpr int BAR = V0 + VS * V_SLOT;
+  static constexpr int NBAR = 1 + 2 * XS + 2 * VS + 3 * NSB + 8 + 1;
   static constexpr int TOTAL = BAR + NBAR * 8 + 16;
   static constexpr uint32_t TX_A = 2u * KB * A_BOX;
-  static constexpr uint32_t TX_STAGE = 2u * KB * XJ_BOX + 4u * V_BOX + 256u;
+  static constexpr uint32_t TX_X = 2u * KB * XJ_BOX;
+  static constexpr uint32_t TX_V = 4u * V_BOX + 256u;
   // TMEM columns
   // per S buffer b: [b*128, +64) the hi.hi product, then K_hi;
   //                 [b*128+64, +64) the hi.lo + lo.hi products, then K_lo
   static constexpr uint32_t T_S = 0;
   static constexpr uint32_t T_X = 64;
-  static constexpr uint32_t T_O = 256;      // 2 epilogue groups x 2 x 2T: O (hh | hi.lo part)
+  static constexpr uint32_t T_O = NSB * 128;  // 2 epilogue groups x 2 x 2T: O (hh | hi.lo part)
   static constexpr uint32_t T_COLS = 512;
+  static_assert(T_O + 8 * T <= T_COLS, "TMEM columns");
+  static_assert(TOTAL + 1024 <= 232448, "shared memory");
 };
 
 struct TcParams {
@@ -231,29 +264,66 @@ struct TcParams {
   float s;
   int sym;
   int tiles_per_split;
-  int split;            // 1: hi/lo products, 0: single tf32 product
   int* status;
 };
 
-template <int DP, int T>
+// MMA1 k-steps KK..DP/8-1 (8 tf32 = 32 B per step inside 128 B atoms).
+template <class Ly, bool SPLIT, int KK, int NK>
+__device__ __forceinline__ void mma1_steps(uint32_t dhh, uint32_t dx, uint64_t dA_hi, uint64_t dA_lo, uint64_t dX,
+                                           uint32_t id1w, uint32_t id1) {
+  if constexpr (KK < NK) {
+    constexpr uint32_t AO = ((KK >> 2) * Ly::A_BOX + (KK & 3) * 32) >> 4;
+    constexpr uint32_t BO = ((KK >> 2) * 2 * Ly::XJ_BOX + (KK & 3) * 32) >> 4;
+    if constexpr (SPLIT) {
+      mma_ss_imm<AO, BO>(dhh, dA_hi, dX, id1w, KK ? 1u : 0u);
+      mma_ss_imm<AO, BO>(dx, dA_lo, dX, id1, 1u);
+    } else {
+      mma_ss_imm<AO, BO>(dhh, dA_hi, dX, id1, KK ? 1u : 0u);
+    }
+    mma1_steps<Ly, SPLIT, KK + 1, NK>(dhh, dx, dA_hi, dA_lo, dX, id1w, id1);
+  }
+}
+// MMA2 k-steps over the 64 columns of the K tile (A = K from TMEM).
+template <class Ly, bool SPLIT, int KK, int NK>
+__device__ __forceinline__ void mma2_steps(uint32_t d, uint32_t khi, uint32_t klo, uint64_t dV, uint32_t id2w,
+                                           uint32_t id2, uint32_t acc0) {
+  if constexpr (KK < NK) {
+    constexpr uint32_t BO = ((KK >> 2) * 2 * Ly::V_BOX + (KK & 3) * 32) >> 4;
+    const uint32_t acc = KK == 0 ? acc0 : 1u;
+    if constexpr (SPLIT) {
+      mma_ts_imm<KK * 8, BO>(d, khi, dV, id2w, acc);
+      mma_ts_imm<KK * 8, BO>(d, klo, dV, id2, 1u);
+    } else {
+      mma_ts_imm<KK * 8, BO>(d, khi, dV, id2, acc);
+    }
+    mma2_steps<Ly, SPLIT, KK + 1, NK>(d, khi, klo, dV, id2w, id2, acc0);
+  }
+}
+
+// SPLIT: hi/lo products (split-TF32); otherwise one TF32 product per term.
+template <int DP, int T, bool SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constant__ CUtensorMap map_r_lo,
               const __grid_constant__ CUtensorMap map_c_hi, const __grid_constant__ CUtensorMap map_c_lo,
               const __grid_constant__ CUtensorMap map_v_hi, const __grid_constant__ CUtensorMap map_v_lo,
               const TcParams p) {
   using Ly = TcLayout<DP, T>;
+  constexpr int NSB = Ly::NSB, XS = Ly::XS, VS = Ly::VS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Ly::BAR);
   uint64_t* bar_a = bars;
-  uint64_t* bar_full = bars + 1;                    // [STAGES]
-  uint64_t* bar_empty = bar_full + Ly::STAGES;      // [STAGES]
-  uint64_t* bar_s = bar_empty + Ly::STAGES;         // [2]    S of group g ready
-  uint64_t* bar_k = bar_s + 2;                      // [2]    K of group g written
-  uint64_t* bar_of = bar_k + 2;                     // [2][2] O of group g, buffer u ready
-  uint64_t* bar_oe = bar_of + 4;                    // [2][2] ... drained
-  uint64_t* bar_fin = bar_oe + 4;                   // MMA pipeline drained
+  uint64_t* bar_xf = bars + 1;              // [XS]   X~_J slot loaded
+  uint64_t* bar_xe = bar_xf + XS;           // [XS]   ... consumed by MMA1
+  uint64_t* bar_vf = bar_xe + XS;           // [VS]   V_J slot (and norms) loaded
+  uint64_t* bar_ve = bar_vf + VS;           // [VS]   ... consumed by MMA2
+  uint64_t* bar_s = bar_ve + VS;            // [NSB]  S in buffer b ready
+  uint64_t* bar_k = bar_s + NSB;            // [NSB]  K in buffer b written
+  uint64_t* bar_kf = bar_k + NSB;           // [NSB]  K in buffer b read by MMA2
+  uint64_t* bar_of = bar_kf + NSB;          // [2][2] O of group g, buffer u ready
+  uint64_t* bar_oe = bar_of + 4;            // [2][2] ... drained
+  uint64_t* bar_fin = bar_oe + 4;           // both MMA issuers drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + Ly::NBAR);
   __shared__ int fail;
 
@@ -268,19 +338,24 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
   if (threadIdx.x == 0) {
     fail = 0;
     mbar_init(bar_a, 1);
-    for (int i = 0; i < Ly::STAGES; ++i) {
-      mbar_init(bar_full + i, 1);
-      mbar_init(bar_empty + i, 1);
+    for (int i = 0; i < XS; ++i) {
+      mbar_init(bar_xf + i, 1);
+      mbar_init(bar_xe + i, 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < VS; ++i) {
+      mbar_init(bar_vf + i, 1);
+      mbar_init(bar_ve + i, 1);
+    }
+    for (int i = 0; i < NSB; ++i) {
       mbar_init(bar_s + i, 1);
       mbar_init(bar_k + i, GROUP_WARPS);
+      mbar_init(bar_kf + i, 1);
     }
     for (int i = 0; i < 4; ++i) {
       mbar_init(bar_of + i, 1);
       mbar_init(bar_oe + i, GROUP_WARPS);
     }
-    mbar_init(bar_fin, 1);
+    mbar_init(bar_fin, 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -297,118 +372,117 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------- TMA producer --
-    mbar_expect_tx(bar_a, Ly::TX_A);
+    mbar_expect_tx(bar_a, SPLIT ? Ly::TX_A : Ly::TX_A / 2);
     for (int kb = 0; kb < Ly::KB; ++kb) {
       tma_2d(smem + Ly::A_HI + kb * Ly::A_BOX, &map_r_hi, bar_a, kb * 32, (int)row0);
-      tma_2d(smem + Ly::A_LO + kb * Ly::A_BOX, p.split ? &map_r_lo : &map_r_hi, bar_a, kb * 32, (int)row0);
+      if (SPLIT) tma_2d(smem + Ly::A_LO + kb * Ly::A_BOX, &map_r_lo, bar_a, kb * 32, (int)row0);
     }
-    int armed = 0;   // tiles whose loads have been issued
+    int armed = 0;   // tiles whose loads (both rings) have been issued
     for (int j = 0; j < ntiles; ++j) {
-      const int st = j % Ly::STAGES;
-      if (j >= Ly::STAGES) {
-        if (!mbar_wait(bar_empty + st, ((j / Ly::STAGES) - 1) & 1, &fail)) break;
-      }
-      uint8_t* sb = smem + Ly::ST0 + st * Ly::STAGE_BYTES;
       const int col0 = (int)((jt0 + j) * BN);
-      mbar_expect_tx(bar_full + st, Ly::TX_STAGE);
+      const int xs = j % XS, vs = j % VS;
+      if (j >= XS && !mbar_wait(bar_xe + xs, ((j / XS) - 1) & 1, &fail)) break;
+      uint8_t* xb = smem + Ly::X0 + xs * Ly::X_SLOT;
+      mbar_expect_tx(bar_xf + xs, SPLIT ? Ly::TX_X : Ly::TX_X / 2);
       for (int kb = 0; kb < Ly::KB; ++kb) {
-        tma_2d(sb + Ly::S_X + (2 * kb) * Ly::XJ_BOX, &map_c_hi, bar_full + st, kb * 32, col0);
-        tma_2d(sb + Ly::S_X + (2 * kb + 1) * Ly::XJ_BOX, p.split ? &map_c_lo : &map_c_hi, bar_full + st,
-               kb * 32, col0);
+        tma_2d(xb + (2 * kb) * Ly::XJ_BOX, &map_c_hi, bar_xf + xs, kb * 32, col0);
+        if (SPLIT) tma_2d(xb + (2 * kb + 1) * Ly::XJ_BOX, &map_c_lo, bar_xf + xs, kb * 32, col0);
       }
-      for (int vb = 0; vb < 2; ++vb) {
-        tma_2d(sb + Ly::S_V + (2 * vb) * Ly::V_BOX, &map_v_hi, bar_full + st, col0 + vb * 32, 0);
-        tma_2d(sb + Ly::S_V + (2 * vb + 1) * Ly::V_BOX, p.split ? &map_v_lo : &map_v_hi, bar_full + st,
-               col0 + vb * 32, 0);
+      if (j >= VS && !mbar_wait(bar_ve + vs, ((j / VS) - 1) & 1, &fail)) {
+        // the X~_J loads of this tile are in flight: let them land first
+        mbar_wait_exit(bar_xf + xs, (j / XS) & 1);
+        break;
       }
-      bulk_g2s(sb + Ly::S_NRM, p.nc + col0, 256, bar_full + st);
+      uint8_t* vb = smem + Ly::V0 + vs * Ly::V_SLOT;
+      mbar_expect_tx(bar_vf + vs, SPLIT ? Ly::TX_V : Ly::TX_V - 2u * Ly::V_BOX);
+      for (int b = 0; b < 2; ++b) {
+        tma_2d(vb + (2 * b) * Ly::V_BOX, &map_v_hi, bar_vf + vs, col0 + b * 32, 0);
+        if (SPLIT) tma_2d(vb + (2 * b + 1) * Ly::V_BOX, &map_v_lo, bar_vf + vs, col0 + b * 32, 0);
+      }
+      bulk_g2s(vb + Ly::V_NRM, p.nc + col0, 256, bar_vf + vs);
       armed = j + 1;
     }
     // never leave with bulk copies still landing in this CTA's memory
     mbar_wait_exit(bar_a, 0);
-    for (int j = max(0, armed - Ly::STAGES); j < armed; ++j)
-      mbar_wait_exit(bar_full + (j % Ly::STAGES), (j / Ly::STAGES) & 1);
-  } else if (warp == 1 && lane == 0) {
-    // ---------------------------------------------------------- MMA issuer --
-    // Tile j belongs to epilogue group g = j & 1 (S/K buffer g), its i-th
-    // tile with i = j >> 1; the group's O accumulates OGROUP of its tiles in
-    // buffer u = (i / OGROUP) & 1.
+    for (int j = max(0, armed - XS); j < armed; ++j) mbar_wait_exit(bar_xf + (j % XS), (j / XS) & 1);
+    for (int j = max(0, armed - VS); j < armed; ++j) mbar_wait_exit(bar_vf + (j % VS), (j / VS) & 1);
+  } else if ((warp == 1 || warp == 3) && lane == 0) {
+    // --------------------------------------------------------- MMA issuers --
+    // Two issuing threads: warp 1 issues MMA1 (cross terms), warp 3 issues
+    // MMA2 (contractions).  Each waits on its own barriers, so one keeps the
+    // tensor pipe fed while the other waits.  Tile j: S/K buffer b = j % NSB,
+    // epilogue group g = j & 1, the group's i-th tile with i = j >> 1; the
+    // group's O accumulates OGROUP of its tiles in buffer u = (i / OGROUP) & 1.
+    // MMA1(j) reuses buffer b only after MMA2(j - NSB) has completed.
     constexpr uint32_t ID1 = idesc_tf32(BM, BN);          // N = 64
     constexpr uint32_t ID1W = idesc_tf32(BM, 2 * BN);     // N = 128: [hi; lo] stacked
     constexpr uint32_t ID2 = idesc_tf32(BM, T);
     constexpr uint32_t ID2W = idesc_tf32(BM, 2 * T);
-    const uint32_t a_hi = su32(smem + Ly::A_HI), a_lo = su32(smem + Ly::A_LO);
+    // SMEM descriptors are built once; an operand at byte offset o from a
+    // 1024-aligned base has descriptor desc(base) + (o >> 4), so every MMA
+    // below issues with constant offsets (a single issuing thread would
+    // otherwise spend tens of cycles per MMA on descriptor arithmetic)
+    const uint64_t dA_hi = sdesc(su32(smem + Ly::A_HI)), dA_lo = sdesc(su32(smem + Ly::A_LO));
+    const uint64_t dX0 = sdesc(su32(smem + Ly::X0)), dV0 = sdesc(su32(smem + Ly::V0));
     bool ok = mbar_wait(bar_a, 0, &fail);
     fence_after();
-    // Columns [g*128, +64) get A_hi B_hi^T and [g*128+64, +64) get
+    // Columns [b*128, +64) get A_hi B_hi^T and [b*128+64, +64) get
     // A_hi B_lo^T + A_lo B_hi^T: one N = 128 MMA writes both halves
     // (B = [hi; lo] rows), a second N = 64 MMA adds A_lo B_hi^T.  Every
     // tcgen05.mma costs a roughly fixed time at small N, so products are
     // stacked along N rather than issued separately.
-    auto mma1 = [&](int j, int buf) {
-      const int st = j % Ly::STAGES;
-      const uint32_t sb = su32(smem + Ly::ST0 + st * Ly::STAGE_BYTES);
-      const uint32_t dhh = tbase + Ly::T_S + buf * 128;
+    auto mma1 = [&](int j) -> bool {
+      const int xs = j % XS, b = j % NSB;
+      if (!mbar_wait(bar_xf + xs, (j / XS) & 1, &fail)) return false;
+      fence_after();
+      const uint64_t dX = dX0 + (uint64_t)(xs * (Ly::X_SLOT >> 4));
+      const uint32_t dhh = tbase + Ly::T_S + b * 128;
       const uint32_t dx = dhh + Ly::T_X;
-      for (int kk = 0; kk < DP / 8; ++kk) {
-        const uint32_t ko = (kk & 3) * 32;   // 8 tf32 = 32 B inside a 128 B atom
-        const uint32_t aoff = (kk >> 2) * Ly::A_BOX + ko;
-        const uint32_t boff = (kk >> 2) * 2 * Ly::XJ_BOX + ko;
-        if (p.split) {
-          mma_ss(dhh, sdesc(a_hi + aoff), sdesc(sb + Ly::S_X + boff), ID1W, kk ? 1u : 0u);
-          mma_ss(dx, sdesc(a_lo + aoff), sdesc(sb + Ly::S_X + boff), ID1, 1u);
-        } else {
-          mma_ss(dhh, sdesc(a_hi + aoff), sdesc(sb + Ly::S_X + boff), ID1, kk ? 1u : 0u);
-        }
-      }
+      mma1_steps<Ly, SPLIT, 0, DP / 8>(dhh, dx, dA_hi, dA_lo, dX, ID1W, ID1);
+      mma_commit(bar_xe + xs);
+      mma_commit(bar_s + b);
+      return true;
     };
     // O[0, T) += K_hi V_hi + K_lo V_hi and O[T, 2T) += K_hi V_lo: the first
     // MMA stacks [V_hi; V_lo] along N (A from TMEM)
-    auto mma2 = [&](int j, int buf, uint32_t ocol, bool first) {
-      const int st = j % Ly::STAGES;
-      const uint32_t sb = su32(smem + Ly::ST0 + st * Ly::STAGE_BYTES);
+    auto mma2 = [&](int j, uint32_t ocol, bool first) -> bool {
+      const int vs = j % VS, b = j % NSB;
+      if (!mbar_wait(bar_vf + vs, (j / VS) & 1, &fail)) return false;
+      fence_after();
+      const uint64_t dV = dV0 + (uint64_t)(vs * (Ly::V_SLOT >> 4));
       const uint32_t d = tbase + ocol;
-      const uint32_t khi = tbase + Ly::T_S + buf * 128, klo = khi + Ly::T_X;
-      for (int kk = 0; kk < BN / 8; ++kk) {
-        const uint32_t boff = (kk >> 2) * 2 * Ly::V_BOX + (kk & 3) * 32;
-        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-        if (p.split) {
-          mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_V + boff), ID2W, acc);
-          mma_ts(d, klo + kk * 8, sdesc(sb + Ly::S_V + boff), ID2, 1u);
-        } else {
-          mma_ts(d, khi + kk * 8, sdesc(sb + Ly::S_V + boff), ID2, acc);
-        }
-      }
+      const uint32_t khi = tbase + Ly::T_S + b * 128, klo = khi + Ly::T_X;
+      mma2_steps<Ly, SPLIT, 0, BN / 8>(d, khi, klo, dV, ID2W, ID2, first ? 0u : 1u);
+      return true;
     };
-    for (int j = 0; ok && j < 2 && j < ntiles; ++j) {
-      if (!(ok = mbar_wait(bar_full + (j % Ly::STAGES), (j / Ly::STAGES) & 1, &fail))) break;
-      fence_after();
-      mma1(j, j & 1);
-      mma_commit(bar_s + (j & 1));
-    }
-    for (int j = 0; ok && j < ntiles; ++j) {
-      const int g = j & 1, i = j >> 1;
-      const int og = i / OGROUP, u = og & 1;
-      const bool first = (i % OGROUP) == 0;
-      const bool last = (i % OGROUP) == OGROUP - 1 || j + 2 >= ntiles;
-      if (!(ok = mbar_wait(bar_k + g, i & 1, &fail))) break;
-      fence_after();
-      if (first && og >= 2) {
-        if (!(ok = mbar_wait(bar_oe + 2 * g + u, ((og - 2) >> 1) & 1, &fail))) break;
-        fence_after();
+    if (warp == 1) {
+      for (int j = 0; ok && j < ntiles; ++j) {
+        const int b = j % NSB;
+        if (j >= NSB) {
+          if (!(ok = mbar_wait(bar_kf + b, ((j / NSB) - 1) & 1, &fail))) break;
+          fence_after();
+        }
+        ok = mma1(j);
       }
-      mma2(j, g, Ly::T_O + (2 * g + u) * 2 * T, first);
-      if (last) mma_commit(bar_of + 2 * g + u);
-      mma_commit(bar_empty + (j % Ly::STAGES));
-      if (j + 2 < ntiles) {
-        const int j2 = j + 2;
-        if (!(ok = mbar_wait(bar_full + (j2 % Ly::STAGES), (j2 / Ly::STAGES) & 1, &fail))) break;
+    } else {
+      for (int j = 0; ok && j < ntiles; ++j) {
+        const int b = j % NSB, g = j & 1, i = j >> 1;
+        const int og = i / OGROUP, u = og & 1;
+        const bool first = (i % OGROUP) == 0;
+        const bool last = (i % OGROUP) == OGROUP - 1 || j + 2 >= ntiles;
+        if (!(ok = mbar_wait(bar_k + b, (j / NSB) & 1, &fail))) break;
         fence_after();
-        mma1(j2, g);
-        mma_commit(bar_s + g);
+        if (first && og >= 2) {
+          if (!(ok = mbar_wait(bar_oe + 2 * g + u, ((og - 2) >> 1) & 1, &fail))) break;
+          fence_after();
+        }
+        if (!(ok = mma2(j, Ly::T_O + (2 * g + u) * 2 * T, first))) break;
+        if (last) mma_commit(bar_of + 2 * g + u);
+        mma_commit(bar_ve + (j % VS));
+        mma_commit(bar_kf + b);
       }
     }
-    // every MMA issued above has completed before TMEM is released
+    // every MMA issued by either thread has completed before TMEM is released
     mma_commit(bar_fin);
     mbar_wait_exit(bar_fin, 0);
   } else if (warp >= EPI_WARP0) {
@@ -445,11 +519,11 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       for (int c8 = 0; c8 < TH; c8 += 8) {
         uint32_t rr[8], rx[8];
         tmem_ld8(oa + c8, rr);
-        if (p.split) tmem_ld8(oa + T + c8, rx);
+        if (SPLIT) tmem_ld8(oa + T + c8, rx);
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-          kahan(c8 + c, __uint_as_float(rr[c]) + (p.split ? __uint_as_float(rx[c]) : 0.f));
+          kahan(c8 + c, __uint_as_float(rr[c]) + (SPLIT ? __uint_as_float(rx[c]) : 0.f));
       }
       fence_before();
       __syncwarp();
@@ -459,32 +533,31 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
     bool ok = true;
     for (int i = 0; i < my_tiles; ++i) {
       const int j = 2 * i + g;
-      const int st = j % Ly::STAGES;
+      const int b = j % NSB, vs = j % VS;
       const int64_t col0 = (jt0 + j) * BN;
-      if (!(ok = mbar_wait(bar_s + g, i & 1, &fail))) break;
-      // the stage's norms: its load completed before MMA1 was issued; the
-      // wait makes the async-proxy writes visible to this thread
-      if (!(ok = mbar_wait(bar_full + st, (j / Ly::STAGES) & 1, &fail))) break;
+      if (!(ok = mbar_wait(bar_s + b, (j / NSB) & 1, &fail))) break;
+      // the slot's norms: the wait makes the async-proxy writes visible here
+      if (!(ok = mbar_wait(bar_vf + vs, (j / VS) & 1, &fail))) break;
       fence_after();
       const bool diag = p.sym && row0 < col0 + BN && col0 < row0 + BM;
-#pragma unroll
+#pragma unroll 1
       for (int half = 0; half < 2; ++half) {
         const int cb = h * 32 + half * 16;   // first of these 16 columns
-        const float4* snb =
-            reinterpret_cast<const float4*>(smem + Ly::ST0 + st * Ly::STAGE_BYTES + Ly::S_NRM) + cb / 4;
-        const uint32_t sa = tbase + lane_off + Ly::T_S + g * 128 + cb;
+        const float4* snb = reinterpret_cast<const float4*>(smem + Ly::V0 + vs * Ly::V_SLOT + Ly::V_NRM) + cb / 4;
+        const uint32_t sa = tbase + lane_off + Ly::T_S + b * 128 + cb;
         uint32_t sh[16], sx[16];
         tmem_ld16(sa, sh);
-        if (p.split) tmem_ld16(sa + Ly::T_X, sx);
+        if (SPLIT) tmem_ld16(sa + Ly::T_X, sx);
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const float4 n4 = snb[c >> 2];      // broadcast load, 4 norms per LDS.128
           const float nbc = (c & 3) == 0 ? n4.x : (c & 3) == 1 ? n4.y : (c & 3) == 2 ? n4.z : n4.w;
           float sab = __uint_as_float(sh[c]);
-          if (p.split) sab += __uint_as_float(sx[c]);
+          if (SPLIT) sab += __uint_as_float(sx[c]);
           const float u2 = fmaxf(fmaf(-2.f, sab, na + nbc), 0.f);
-          const float uu = sqrt_approx(u2);
+          // u = u2 / sqrt(u2) with one MUFU op; the floor keeps u2 = 0 at 0
+          const float uu = u2 * rsqrt_approx(fmaxf(u2, 1e-30f));
           const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
           // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder
           // (|lo| <= 2^-11 |K|, so kind::tf32 reading lo costs <= 2^-22 |K|)
@@ -504,12 +577,12 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
           }
         }
         tmem_st16(sa, sh);
-        if (p.split) tmem_st16(sa + Ly::T_X, sx);
+        if (SPLIT) tmem_st16(sa + Ly::T_X, sx);
       }
       tmem_wait_st();
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar_k + g);
+      if (lane == 0) mbar_arrive(bar_k + b);
       // drain this group's previous O buffer once its last MMA2 was issued
       if ((i % OGROUP) == 0 && i > 0 && !(ok = drain(i / OGROUP - 1))) break;
     }
@@ -581,7 +654,7 @@ int make_map(gp_ctx* ctx, CUtensorMap* m, const float* base, int64_t rows, int64
   return GP_OK;
 }
 
-template <int DP, int T>
+template <int DP, int T, bool SPLIT>
 int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi, const float* vlo,
               int64_t vld, int t, float* out, int64_t ldo, float s, bool sym, bool split, int* status) {
   using Ly = TcLayout<DP, T>;
@@ -597,7 +670,7 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   const size_t smem = Ly::TOTAL + 1024;
   static bool attr = false;
   if (!attr) {
-    GP_CUDA(ctx, cudaFuncSetAttribute(kmv_tc_kernel<DP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GP_CUDA(ctx, cudaFuncSetAttribute(kmv_tc_kernel<DP, T, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     attr = true;
   }
@@ -618,9 +691,8 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   prm.s = s;
   prm.sym = sym ? 1 : 0;
   prm.tiles_per_split = (int)per;
-  prm.split = split ? 1 : 0;
   prm.status = status;
-  kmv_tc_kernel<DP, T><<<dim3((unsigned)row_tiles, (unsigned)splits), NTHREADS, smem, ctx->stream>>>(
+  kmv_tc_kernel<DP, T, SPLIT><<<dim3((unsigned)row_tiles, (unsigned)splits), NTHREADS, smem, ctx->stream>>>(
       mrh, mrl, mch, mcl, mvh, mvl, prm);
   GP_LAUNCHED(ctx);
   return GP_OK;
@@ -681,12 +753,21 @@ int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V, int6
     GP_LAUNCHED(ctx);
     float* oc = out + (int64_t)c0 * ldo;
     int rc;
-    if (rows.d_pad == 32)
-      rc = T == 16 ? launch_tc<32, 16>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status)
-                   : launch_tc<32, 32>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status);
-    else
-      rc = T == 16 ? launch_tc<64, 16>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status)
-                   : launch_tc<64, 32>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, split, status);
+    if (split) {
+      if (rows.d_pad == 32)
+        rc = T == 16 ? launch_tc<32, 16, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status)
+                     : launch_tc<32, 32, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status);
+      else
+        rc = T == 16 ? launch_tc<64, 16, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status)
+                     : launch_tc<64, 32, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status);
+    } else {
+      if (rows.d_pad == 32)
+        rc = T == 16 ? launch_tc<32, 16, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status)
+                     : launch_tc<32, 32, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status);
+      else
+        rc = T == 16 ? launch_tc<64, 16, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status)
+                     : launch_tc<64, 32, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status);
+    }
     if (rc != GP_OK) return rc;
   }
   return GP_OK;
