@@ -30,26 +30,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "mBCG solve s at N=1M (mixed vs FP32, 1e-4 resid); K̂·V TFLOP/s; p50/p99 ms"
 WORKLOADS = {
-    # name: (synth recipe, probes, rank, tol, max_iter)
-    "gp1m": ("gp1m", 15, 100, 1e-4, 400),
-    "gp256k": ("gp256k", 31, 64, 1e-4, 400),
-    "gp64k": ("gp64k", 31, 64, 1e-4, 1500),
-    "gp2k": ("gp2k", 15, 32, 1e-6, 1000),
+    # name: (synth recipe, probes, rank, tol, max_iter, preconditioner form)
+    # gp1m/gp256k: clustered features with a near-diagonal K, where the
+    # residual-diagonal form of the rank-k preconditioner is the one that
+    # converges (the sigma^2 I form needs > 400 steps at k = 100)
+    "gp1m": ("gp1m", 15, 100, 1e-4, 400, "resid"),
+    "gp256k": ("gp256k", 31, 64, 1e-4, 400, "resid"),
+    "gp64k": ("gp64k", 31, 64, 1e-4, 1500, "sigma"),
+    "gp2k": ("gp2k", 15, 32, 1e-6, 1000, "sigma"),
 }
 # K-hat products one solve of each workload needs (split-TF32 path, seed 0);
 # the reference arm scales its per-product oracle time by this count.
-PRODUCTS_PER_SOLVE = {"gp1m": 131, "gp256k": 120, "gp64k": 1200, "gp2k": 60}
+PRODUCTS_PER_SOLVE = {"gp1m": 97, "gp256k": 120, "gp64k": 1200, "gp2k": 60}
+# DRAM bytes per launch of the fused tensor-core K-hat V kernel from one ncu
+# capture (profiles/kmv_tc_gp1m.md); None until the current kernel is captured.
+KMV_DRAM_BYTES = {}
+# TF32 dense tensor peak from the measured BF16 one, by the nominal ratio
+# 1.1 / 2.25 PFLOP/s
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gp1m", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="split_tf32",
                     choices=["fp32", "split_tf32", "split_bf16", "tf32", "bf16"])
+    ap.add_argument("--precond", default="auto", choices=["auto", "sigma", "resid"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -123,20 +133,35 @@ def load_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def pipe_peak_tflops(precision: str, d: int, t: int, sm_mhz: float, n_sm: int = 152):
-    """GEMM-equivalent TFLOP/s at the bound of the busiest pipe, per kernel
-    entry: the plain form issues d + t + 12 FP32 ops on 128 lanes per SM-clock;
-    the tensor forms issue 2 MUFU ops (sqrt, exp2) on 16 lanes per SM-clock and
-    ~10 FP32 ops, with both contractions on the tensor pipe.  Returns
-    (peak TFLOP/s, bound name, entries/s at the bound)."""
-    clk = sm_mhz * 1e6
+def tensor_flops_per_entry(precision: str, d: int, t: int) -> float:
+    """Tensor-pipe work per kernel entry of one K-hat V product: the cross
+    term (2d) and the contraction (2t), each as three TF32 products in the
+    split form (hi.hi + hi.lo + lo.hi) and one in the single TF32 form."""
+    per = 2.0 * (d + t)
+    return 3.0 * per if precision == "split_tf32" else per
+
+
+def roofline(precision: str, d: int, t: int, entries_per_s: float, sm_mhz: float, peaks: dict,
+             peak_src: str, n_sm: int = 152):
+    """Roofline of the fused K-hat V kernel.
+
+    Tensor-core forms: achieved = N^2 x tensor FLOPs per entry / kernel time,
+    against the dense TF32 peak (measured BF16 burst x 1.1/2.25).  Plain FP32
+    form: bound by the FMA/ALU pipes at d + t + 12 FP32 ops per entry on 128
+    lanes per SM-clock (derived; no measured FP32 peak)."""
     if precision == "fp32":
-        ent = n_sm * 128 * clk / (d + t + 12)
-        bound = "fp32"
-    else:
-        ent = min(n_sm * 16 * clk / 2.0, n_sm * 128 * clk / 10.0)
-        bound = "sfu"
-    return 2.0 * (d + t) * ent / 1e12, bound, ent
+        ops = d + t + 12
+        achieved = entries_per_s * ops / 1e12
+        peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "per_entry": f"{ops} FP32 ops",
+                "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)"}
+    fl = tensor_flops_per_entry(precision, d, t)
+    achieved = entries_per_s * fl / 1e12
+    peak = peaks["bf16_tflops"] * TF32_PER_BF16
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "per_entry": f"{fl:.0f} tensor FLOPs",
+            "peak_basis": f"TF32 = BF16 burst {peaks['bf16_tflops']} ({peak_src}) x 1.1/2.25"}
 
 
 def cpu_baseline(w, t, n_products, budget_s=12.0):
@@ -147,11 +172,13 @@ def cpu_baseline(w, t, n_products, budget_s=12.0):
     from oracle import gp_oracle as go
     rng = np.random.default_rng(0)
     V = rng.choice([-1.0, 1.0], size=(w.N, t))
-    probe = np.sort(rng.choice(w.N, size=4, replace=False))
+    # per-row cost from a warm 16-row probe, then a sample sized to the budget
+    go.khat_matmul_rows(w.X, V, w.lengthscale, 1.0, w.sigma2, np.arange(2))
+    probe = np.sort(rng.choice(w.N, size=16, replace=False))
     t0 = time.perf_counter()
     go.khat_matmul_rows(w.X, V, w.lengthscale, 1.0, w.sigma2, probe)
     per_row = (time.perf_counter() - t0) / len(probe)
-    nrows = int(max(4, min(4096, w.N, budget_s / max(per_row, 1e-9))))
+    nrows = int(max(16, min(8192, w.N, budget_s / max(per_row, 1e-9))))
     rows = np.sort(rng.choice(w.N, size=nrows, replace=False))
     t0 = time.perf_counter()
     go.khat_matmul_rows(w.X, V, w.lengthscale, 1.0, w.sigma2, rows)
@@ -170,7 +197,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from synth import make_workload
-    recipe, npr, k, tol, maxit = WORKLOADS[args.workload]
+    recipe, npr, k, tol, maxit, _pc = WORKLOADS[args.workload]
     w = make_workload(recipe, seed=None)
     t = 1 + npr
     nprod = PRODUCTS_PER_SOLVE[args.workload]
@@ -210,7 +237,10 @@ def run_ours(args):
     import paper_2109_09817_gb300 as gp
     from synth import make_workload
 
-    recipe, npr, k, tol, maxit = WORKLOADS[args.workload]
+    recipe, npr, k, tol, maxit, pc_name = WORKLOADS[args.workload]
+    if args.precond != "auto":
+        pc_name = args.precond
+    pc = gp.GP_PC_RESID if pc_name == "resid" else gp.GP_PC_SIGMA
     w = make_workload(recipe, seed=None if rank == 0 else 100 + rank)
     t = 1 + npr
     prec = gp.PRECISIONS[args.precision]
@@ -225,7 +255,7 @@ def run_ours(args):
     def step(Xd, yd):
         return gp.gp_logml_and_grad(ctx, Xd, theta, yd, n_probes=npr, seed=args.seed, k=k,
                                     tol=tol, max_iter=maxit, precision=prec,
-                                    allow_notconv=True)
+                                    allow_notconv=True, precond=pc)
 
     def barrier():
         torch.cuda.synchronize()
@@ -290,16 +320,17 @@ def run_ours(args):
 
     r = results[-1]
     kmv_ms = kms.value / max(nprod.value, 1)
-    achieved = kfl.value / max(nprod.value, 1) / (kmv_ms * 1e-3) / 1e12 if nprod.value else 0.0
+    ent_s = kel.value / max(nprod.value, 1) / (kmv_ms * 1e-3) if nprod.value else 0.0
     peaks, peak_src = load_peaks()
     sm = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak, pipe, ent_bound = pipe_peak_tflops(args.precision, w.d, t, sm)
-    roof = {"bound": "alu", "pipe": pipe, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None, "traffic": None,
-            "kernel": "K-hat V (fused)", "per_launch_ms": kmv_ms,
-            "entries_per_s": kel.value / max(nprod.value, 1) / (kmv_ms * 1e-3) if nprod.value else 0.0,
-            "peak_basis": f"pipe counts x median SM clock {sm:.0f} MHz under load (derived; "
-                          f"MEASURED_PEAKS.json {peak_src} for HBM/bf16)"}
+    roof = roofline(args.precision, w.d, t, ent_s, sm, peaks, peak_src)
+    roof.update({"traffic": KMV_DRAM_BYTES.get((args.workload, args.precision)),
+                 "kernel": "fused K-hat V (kmv_tc_kernel)" if args.precision != "fp32"
+                 else "fused K-hat V (kmv_plain_kernel)",
+                 "per_launch_ms": kmv_ms, "launches": int(nprod.value),
+                 "entries_per_s": ent_s,
+                 "gemm_equiv_tflops": ent_s * 2.0 * (w.d + t) / 1e12,
+                 "timing": "CUDA events around every K-hat V product on the context stream"})
     if rank != 0:
         return 0
     cb = None
@@ -314,7 +345,7 @@ def run_ours(args):
                   "tf32": "tf32/f32", "bf16": "bf16/f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: N={w.N}, d={w.d}, t=1+{npr}, k={k}, tol={tol}",
-                   "precision": args.precision,
+                   "precision": args.precision, "preconditioner": f"rank {k}, {pc_name} form",
                    "step": "prep + pivoted Cholesky + probes + mBCG + Lanczos log-det + gradient",
                    "l2": f"inputs larger than L2 (X {w.X.nbytes / 2**20:.0f} MiB)",
                    "parallelism": f"replicas x{world}"},
