@@ -109,3 +109,24 @@ def test_ard_scale_invariance():
     K1 = go.kernel_matrix(X, X, ell, 1.0)
     K2 = go.kernel_matrix(X * c, X * c, ell * c, 1.0)
     np.testing.assert_allclose(K1, K2, rtol=1e-14, atol=1e-15)
+
+
+def test_true_relative_residual_vs_brute_force():
+    """The solve checker: ||K-hat w - b|| / ||b|| per column with K-hat from
+    brute-force loops, full and on a row sample."""
+    rng = np.random.default_rng(14)
+    N, d = 21, 3
+    X = rng.standard_normal((N, d)).astype(np.float32)
+    ell = rng.uniform(0.5, 2.0, d)
+    Kh = _brute_kernel(X, X, ell, 0.9) + 1e-2 * np.eye(N)
+    W = rng.standard_normal((N, 2))
+    B = Kh @ W + 1e-3 * rng.standard_normal((N, 2))
+    ref = np.linalg.norm(Kh @ W - B, axis=0) / np.linalg.norm(B, axis=0)
+    np.testing.assert_allclose(go.true_relative_residual(X, ell, 0.9, 1e-2, W, B), ref,
+                               rtol=1e-9)
+    rows = np.array([0, 3, 7, 20])
+    refr = np.linalg.norm((Kh @ W - B)[rows], axis=0) / np.linalg.norm(B[rows], axis=0)
+    np.testing.assert_allclose(go.true_relative_residual(X, ell, 0.9, 1e-2, W, B, rows), refr,
+                               rtol=1e-9)
+    # the exact solution has zero residual
+    assert go.true_relative_residual(X, ell, 0.9, 1e-2, np.linalg.solve(Kh, B), B).max() < 1e-10
