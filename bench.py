@@ -42,9 +42,10 @@ WORKLOADS = {
 # K-hat products one solve of each workload needs (split-TF32 path, seed 0);
 # the reference arm scales its per-product oracle time by this count.
 PRODUCTS_PER_SOLVE = {"gp1m": 97, "gp256k": 120, "gp64k": 1200, "gp2k": 60}
-# DRAM bytes per launch of the fused tensor-core K-hat V kernel from one ncu
-# capture (profiles/kmv_tc_gp1m.md); None until the current kernel is captured.
-KMV_DRAM_BYTES = {}
+# DRAM bytes (read + write) per launch of the fused tensor-core K-hat V kernel
+# from one ncu capture of the full-size launch (profiles/kmv_tc_gp1m.md);
+# entries are removed whenever the kernel changes after the capture.
+KMV_DRAM_BYTES = {("gp1m", "split_tf32"): 15.04e9 + 0.965e9}
 # TF32 dense tensor peak from the measured BF16 one, by the nominal ratio
 # 1.1 / 2.25 PFLOP/s
 TF32_PER_BF16 = 1.1 / 2.25
@@ -191,6 +192,24 @@ def cpu_baseline(w, t, n_products, budget_s=12.0):
                        f"and by {n_products} products per solve")}
 
 
+# ------------------------------------------------------------ replicas ----
+def replica_seed(rank: int):
+    """Rank 0 solves the workload's own seeded problem, rank r > 0 the
+    problem seeded 100 + r (independent replicas; nothing is exchanged)."""
+    return None if rank == 0 else 100 + rank
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """Max of a per-rank scalar over all ranks (the slowest rank sets the
+    step time); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+    tt = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 # ----------------------------------------------------------- reference ----
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -241,7 +260,7 @@ def run_ours(args):
     if args.precond != "auto":
         pc_name = args.precond
     pc = gp.GP_PC_RESID if pc_name == "resid" else gp.GP_PC_SIGMA
-    w = make_workload(recipe, seed=None if rank == 0 else 100 + rank)
+    w = make_workload(recipe, seed=replica_seed(rank))
     t = 1 + npr
     prec = gp.PRECISIONS[args.precision]
     theta = gp.Theta(w.lengthscale, w.outputscale, w.sigma2)
@@ -291,11 +310,7 @@ def run_ours(args):
     ctx.lib.gp_profile_read(ctx.h, ctypes.byref(nprod), ctypes.byref(kms), ctypes.byref(kfl),
                             ctypes.byref(kel))
     ctx.lib.gp_profile(ctx.h, 0)
-    ms_step = ms_total / args.steps
-    if dist:
-        tt = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = max_over_ranks(ms_total / args.steps, dist, "cuda")
 
     # end to end: host inputs copied in every step, results read back
     e2e = None
@@ -309,11 +324,7 @@ def run_ours(args):
             yd.copy_(yh, non_blocking=True)
             step(Xd, yd)   # returns host scalars and gradient (synchronises)
         barrier()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
         e2e = {"value": e2e_s / max(world, 1), "unit": "s",
                "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 4),
                "d2h_bytes_per_step": int(8 * (w.d + 2 + 3))}

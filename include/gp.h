@@ -178,6 +178,31 @@ GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
             double* alpha_hist, double* beta_hist, int* iters,
             double* rel_resid);
 
+/* Mixed-precision iterative refinement of K-hat Omega = B (the solve of
+ * Sec. 3.1; the refinement loop itself is not in the paper).  Starting from
+ * Omega = 0: solve K-hat delta = R with preconditioned mBCG whose products use
+ * `inner_precision` (e.g. GP_TF32), to relative residual `inner_tol`; then
+ * Omega += delta and R = B - K-hat Omega with products in `outer_precision`
+ * (GP_FP32_SPLIT_TF32 or GP_FP32_PLAIN).  A column stops once
+ * ||R_c|| / ||B_c|| < tol (its R is zeroed, so later inner solves skip it);
+ * the loop ends when every column has stopped or after max_outer rounds.
+ * Preconditioner as in gp_mbcg (L, k, resid_diag).  B, Omega: device, N x t
+ * column-major (ld N).  outer_steps, inner_steps (total inner CG steps over
+ * all rounds, max over columns per round), rel_resid (t, the last true
+ * relative residuals in the outer precision): nullable HOST outputs.
+ * Returns GP_ENOTCONV (Omega holds the last iterate) when a column has not
+ * reached tol after max_outer rounds.  If an inner solve breaks down (the
+ * inner operator is too inexact to stay positive definite, e.g. single TF32
+ * on near-duplicate rows) its partial iterate is used; a round that breaks
+ * down and reduces no residual by 10 % returns GP_EBREAKDOWN.  Synchronises
+ * once per round. */
+GP_API int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
+                   const gp_theta* theta, const double* L, int k,
+                   const double* resid_diag, const float* B, int t, double tol,
+                   double inner_tol, int max_outer, int max_iter,
+                   int inner_precision, int outer_precision, float* Omega,
+                   int* outer_steps, int* inner_steps, double* rel_resid);
+
 /* ---- log marginal likelihood and gradient (Eq. ll; Sec. 3.2) -------------
  * One pass of the whole training path: rank-k pivoted Cholesky and the
  * preconditioner P = L L^T + D of form `precond` (GP_PC_SIGMA or
@@ -244,6 +269,57 @@ GP_API void gp_model_free(gp_model* model);
  * floats.  Synchronises when var is requested. */
 GP_API int gp_predict(gp_ctx* ctx, const gp_model* model, const float* Xp, int64_t M,
                float* mean, float* var, int var_mode);
+
+/* ---- serving: continuous batching over resident models (Eq. pred) --------
+ * A gp_server holds trained models on one device and serves two request
+ * kinds from host memory:
+ *  - predict: the mean K(X', X) a of one request's M feature rows against a
+ *    resident model.  Each model has its own stream and batching thread:
+ *    every request queued when a batch starts (up to max_batch_rows rows) is
+ *    packed into ONE fused K(X', X) a launch; requests arriving meanwhile join
+ *    the next batch.  Batches of different models overlap on the device.
+ *  - solve: a new model's a = K-hat^{-1} y (split-TF32 mBCG, rank-k
+ *    residual-diagonal preconditioner), on its own stream, overlapping the
+ *    predict batches; admitted when the device's free memory covers the
+ *    solve's estimated footprint plus reserve_bytes (waits up to ~60 s, then
+ *    the request fails with GP_ENOMEM).
+ * Host arrays passed to gp_server_predict / gp_server_solve must stay valid
+ * until gp_server_wait for that ticket has returned.  The server object is
+ * thread-safe: requests may be submitted and waited for from any thread. */
+typedef struct gp_server gp_server;
+
+/* device: CUDA device index; max_batch_rows >= 1: row budget of one predict
+ * batch (a single request may not exceed it); reserve_bytes >= 0: device
+ * memory kept free when admitting a solve.  GP_ECUDA if the device or its
+ * streams cannot be set up. */
+GP_API int gp_server_create(gp_server** out, int device, int64_t max_batch_rows,
+                            double reserve_bytes);
+/* Fit a model from DEVICE arrays X (N x d) and y (N) as gp_model_fit does,
+ * keep it resident and start its batching thread; *model_id is its index.
+ * Synchronises; errors as gp_model_fit (message in gp_server_last_error). */
+GP_API int gp_server_add_model(gp_server* srv, const float* X, int64_t N, int d,
+                               const gp_theta* theta, const float* y, int k, int precond,
+                               double tol, int max_iter, int precision, int* model_id);
+/* Queue a predict request: Xp HOST M x d row-major, mean HOST M floats
+ * (written before the request completes).  GP_EINVAL for an unknown model,
+ * M < 1 or M > max_batch_rows. */
+GP_API int gp_server_predict(gp_server* srv, int model_id, const float* Xp, int64_t M,
+                             float* mean, uint64_t* ticket);
+/* Queue a solve request: X HOST N x d, y HOST N, alpha HOST N (out). */
+GP_API int gp_server_solve(gp_server* srv, const float* X, int64_t N, int d,
+                           const gp_theta* theta, const float* y, int k, double tol,
+                           int max_iter, float* alpha, uint64_t* ticket);
+/* Wait up to timeout_s seconds for a request; returns its status (GP_OK or
+ * the error it failed with), GP_ETIMEOUT if it has not completed (the ticket
+ * stays valid), GP_EINVAL for an unknown ticket.  latency_ms (nullable HOST):
+ * submit-to-completion time.  A completed ticket is released. */
+GP_API int gp_server_wait(gp_server* srv, uint64_t ticket, double timeout_s,
+                          double* latency_ms);
+/* Predict batches launched and predict requests served so far. */
+GP_API int gp_server_stats(gp_server* srv, int64_t* batches, int64_t* predicted);
+GP_API const char* gp_server_last_error(gp_server* srv);
+/* Finishes every queued request, then frees models, streams and buffers. */
+GP_API void gp_server_destroy(gp_server* srv);
 
 #ifdef __cplusplus
 }

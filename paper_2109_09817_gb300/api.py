@@ -186,6 +186,36 @@ def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tenso
                 relres=np.array(rr[:]), rc=rc)
 
 
+def gp_mbcg_refine(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tensor],
+                   B: torch.Tensor, tol: float = 1e-4, inner_tol: float = 1e-2,
+                   max_outer: int = 10, max_iter: int = 1000,
+                   inner_precision: int = GP_TF32, outer_precision: int = GP_FP32_SPLIT_TF32,
+                   resid: Optional[torch.Tensor] = None, allow_notconv: bool = False):
+    """Mixed-precision iterative refinement of K-hat Omega = B; returns
+    dict(Omega, outer, inner, relres, rc)."""
+    _dev(ctx, X, torch.float32, "X")
+    N, d = X.shape
+    B = _block(ctx, B, N, "B")
+    t = B.shape[0]
+    k = 0 if L is None else L.shape[0]
+    if L is not None:
+        _dev(ctx, L, torch.float64, "L")
+    if resid is not None:
+        _dev(ctx, resid, torch.float64, "resid")
+    Om = torch.empty_like(B)
+    outer = ctypes.c_int(0)
+    inner = ctypes.c_int(0)
+    rr = (ctypes.c_double * t)()
+    th, keep = theta.as_c()
+    allow = (GP_ENOTCONV,) if allow_notconv else ()
+    rc = ctx.check(ctx.lib.gp_mbcg_refine(ctx.h, _p(X), N, d, ctypes.byref(th), _p(L), k, _p(resid),
+                                          _p(B), t, tol, inner_tol, max_outer, max_iter,
+                                          inner_precision, outer_precision, _p(Om),
+                                          ctypes.byref(outer), ctypes.byref(inner), rr),
+                   allow=allow)
+    return dict(Omega=Om, outer=outer.value, inner=inner.value, relres=np.array(rr[:]), rc=rc)
+
+
 def gp_logml_and_grad(ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tensor,
                       n_probes: int = 15, seed: int = 0, k: int = 32, tol: float = 1e-6,
                       max_iter: int = 1000, precision: int = GP_FP32_PLAIN,
@@ -254,3 +284,91 @@ def gp_predict(ctx: Context, model: Model, Xp: torch.Tensor, var_mode: int = GP_
     var = torch.empty(M, dtype=torch.float32, device=Xp.device) if var_mode else None
     ctx.check(ctx.lib.gp_predict(ctx.h, model.h, _p(Xp), M, _p(mean), _p(var), var_mode))
     return mean, var
+
+
+class Server:
+    """Continuous-batching request loop over resident models (gp_server_*).
+
+    predict()/solve() take host numpy arrays and return a ticket; wait()
+    returns (status, latency_ms).  The arrays are kept alive here until their
+    request has been waited for."""
+
+    def __init__(self, device: int = 0, max_batch_rows: int = 65536, reserve_bytes: float = 0.0):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        rc = self.lib.gp_server_create(ctypes.byref(h), device, max_batch_rows, reserve_bytes)
+        if rc != GP_OK:
+            raise GPError(rc, "gp_server_create failed")
+        self.h = h
+        self.device = device
+        self._keep = {}
+
+    def check(self, rc: int):
+        if rc != GP_OK:
+            raise GPError(rc, self.lib.gp_server_last_error(self.h).decode())
+        return rc
+
+    def add_model(self, X: torch.Tensor, theta: Theta, y: torch.Tensor, k: int = 32,
+                  precond: int = GP_PC_RESID, tol: float = 1e-4, max_iter: int = 1000,
+                  precision: int = GP_FP32_SPLIT_TF32) -> int:
+        if not (X.is_cuda and y.is_cuda):
+            raise ValueError("add_model takes device tensors")
+        N, d = X.shape
+        mid = ctypes.c_int(-1)
+        th, keep = theta.as_c()
+        self.check(self.lib.gp_server_add_model(self.h, _p(X), N, d, ctypes.byref(th), _p(y), k,
+                                                precond, tol, max_iter, precision,
+                                                ctypes.byref(mid)))
+        return mid.value
+
+    def predict(self, model_id: int, Xp: np.ndarray):
+        Xp = np.ascontiguousarray(Xp, dtype=np.float32)
+        mean = np.empty(Xp.shape[0], dtype=np.float32)
+        tk = ctypes.c_uint64()
+        self.check(self.lib.gp_server_predict(self.h, model_id, Xp.ctypes.data_as(ctypes.c_void_p),
+                                              Xp.shape[0], mean.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.byref(tk)))
+        self._keep[tk.value] = (Xp, mean)
+        return tk.value
+
+    def solve(self, X: np.ndarray, theta: Theta, y: np.ndarray, k: int = 32, tol: float = 1e-4,
+              max_iter: int = 1000):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        alpha = np.empty(X.shape[0], dtype=np.float32)
+        th, ell = theta.as_c()
+        tk = ctypes.c_uint64()
+        self.check(self.lib.gp_server_solve(self.h, X.ctypes.data_as(ctypes.c_void_p), X.shape[0],
+                                            X.shape[1], ctypes.byref(th),
+                                            y.ctypes.data_as(ctypes.c_void_p), k, tol, max_iter,
+                                            alpha.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(tk)))
+        self._keep[tk.value] = (X, y, alpha, ell)
+        return tk.value
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        """Returns (status, latency_ms, result array)."""
+        lat = ctypes.c_double(0.0)
+        rc = self.lib.gp_server_wait(self.h, ctypes.c_uint64(ticket), timeout_s, ctypes.byref(lat))
+        if rc == _lib.GP_ETIMEOUT:
+            return rc, None, None
+        kept = self._keep.pop(ticket, None)
+        out = None if kept is None else kept[1] if len(kept) == 2 else kept[2]
+        return rc, lat.value, out
+
+    def stats(self):
+        b, p = ctypes.c_int64(), ctypes.c_int64()
+        self.check(self.lib.gp_server_stats(self.h, ctypes.byref(b), ctypes.byref(p)))
+        return {"batches": b.value, "predicted": p.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gp_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

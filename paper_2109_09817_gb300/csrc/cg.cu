@@ -384,6 +384,28 @@ int copy_vectors(gp_ctx* ctx, const float* src, int64_t lds, float* dst,
   return GP_OK;
 }
 
+namespace {
+__global__ void axpby_kernel(float a, const float* X, float b, const float* Y, float* out, int64_t ld,
+                             int64_t n, int t) {
+  const int64_t total = n * t;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / n, r = i % n;
+    const int64_t o = c * ld + r;
+    out[o] = fmaf(a, X[o], b * Y[o]);
+  }
+}
+}  // namespace
+
+int axpby_vectors(gp_ctx* ctx, float a, const float* X, float b, const float* Y, float* out,
+                  int64_t ld, int64_t n, int t) {
+  const int64_t total = n * t;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 16LL * ctx->num_sms));
+  axpby_kernel<<<g, 256, 0, ctx->stream>>>(a, X, b, Y, out, ld, n, t);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
 int dot_columns(gp_ctx* ctx, const float* A, const float* B, int64_t ld,
                 int64_t n, int t, double* out) {
   double* part = ws<double>(ctx, WS_PART, (size_t)kRedBlocks * t);

@@ -8,29 +8,6 @@
 
 #include "gp_internal.cuh"
 
-struct gp_model {
-  int device = 0;
-  int64_t n = 0, n_pad = 0;
-  int d = 0, d_pad = 0;
-  int precision = GP_FP32_PLAIN;
-  std::vector<double> ell;
-  double s = 1.0, sigma2 = 1e-4, tol = 1e-6;
-  int max_iter = 1000;
-  double* mu = nullptr;
-  float* xt = nullptr;
-  float* norm = nullptr;
-  float* xt_hi = nullptr;
-  float* xt_lo = nullptr;
-  __nv_bfloat16* xb_hi = nullptr;
-  __nv_bfloat16* xb_lo = nullptr;
-  float* alpha = nullptr;      // n_pad, zero padded
-  double* L = nullptr;         // n x k
-  int k = 0;
-  float* L32 = nullptr;
-  double* cfac = nullptr;
-  float* dh = nullptr;         // D^{-1/2}, n_pad
-  double pc_logdet = 0.0;
-};
 
 namespace gp {
 
@@ -317,6 +294,122 @@ int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
   }
   if (res.breakdown) return set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown (loss of definiteness)");
   if (!res.converged) return set_err(ctx, GP_ENOTCONV, "mBCG: max_iter=%d reached", max_iter);
+  return GP_OK;
+}
+
+int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
+                   const gp_theta* theta, const double* L, int k,
+                   const double* resid_diag, const float* B, int t, double tol,
+                   double inner_tol, int max_outer, int max_iter,
+                   int inner_precision, int outer_precision, float* Omega,
+                   int* outer_steps, int* inner_steps, double* rel_resid) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (!B || !Omega || t < 1 || t > kMaxT || max_iter < 1 || max_outer < 1 || !(tol > 0.0) ||
+      !(inner_tol > 0.0) || k < 0 || (k > 0 && !L) || !valid_precision(inner_precision) ||
+      (outer_precision != GP_FP32_PLAIN && outer_precision != GP_FP32_SPLIT_TF32))
+    return set_err(ctx, GP_EINVAL, "gp_mbcg_refine: bad arguments");
+  cudaStream_t st = ctx->stream;
+  // outer products on the accurate features, inner ones on a second family
+  Prep po, pi;
+  GP_TRY(prep_train(ctx, X, N, d, theta, outer_precision, &po));
+  const double* mu = static_cast<const double*>(ctx->ws[WS_MU].p);
+  GP_TRY(prepare_features(ctx, X, N, d, mu, theta->lengthscale, inner_precision, WS_XT2, &pi));
+  Precond pc;
+  GP_TRY(precond_setup(ctx, L, N, k, k, theta->sigma2, resid_diag, &pc));
+  const size_t nv = (size_t)t * N;
+  float* R = ws<float>(ctx, WS_RF_R, nv);
+  float* Dl = ws<float>(ctx, WS_RF_D, nv);
+  float* W = ws<float>(ctx, WS_RF_W, nv);
+  double* ah = ws<double>(ctx, WS_CG_AH, (size_t)max_iter * t);
+  double* bh = ws<double>(ctx, WS_CG_BH, (size_t)max_iter * t);
+  double* sm = ws<double>(ctx, WS_RF_S, (size_t)4 * t + 16);
+  if (!R || !Dl || !W || !ah || !bh || !sm) return set_err(ctx, GP_ENOMEM, "workspace (refinement)");
+  double* bb = sm;              // ||B_c||^2
+  double* rr = sm + t;          // ||R_c||^2
+  double* rr_dev = sm + 2 * t;  // inner relres (unused)
+  int* it_dev = reinterpret_cast<int*>(sm + 3 * t);
+  double* h = static_cast<double*>(pinned_get(ctx, sizeof(double) * 2 * t));
+  if (!h) return set_err(ctx, GP_ENOMEM, "pinned staging");
+  GP_TRY(dot_columns(ctx, B, B, N, N, t, bb));
+  GP_CUDA(ctx, cudaMemsetAsync(Omega, 0, sizeof(float) * nv, st));
+  GP_TRY(copy_vectors(ctx, B, N, R, N, N, t, 1.f));
+  std::vector<double> bnorm(t), rel(t, 1.0);
+  std::vector<char> done(t, 0);
+  int outer = 0, inner = 0;
+  bool all = false;
+  for (int c = 0; c < t; ++c) rel[c] = 1.0;
+  GP_CUDA(ctx, cudaMemcpyAsync(h, bb, sizeof(double) * t, cudaMemcpyDeviceToHost, st));
+  GP_CUDA(ctx, cudaStreamSynchronize(st));
+  for (int c = 0; c < t; ++c) {
+    bnorm[c] = std::sqrt(h[c]);
+    if (bnorm[c] == 0.0) {   // zero right-hand side: Omega_c = 0 is exact
+      done[c] = 1;
+      rel[c] = 0.0;
+    }
+  }
+  while (outer < max_outer) {
+    all = true;
+    for (int c = 0; c < t; ++c) all = all && done[c];
+    if (all) break;
+    // inner solve K-hat delta = R in the inner precision
+    CgArgs a;
+    a.prep = &pi;
+    a.s = theta->outputscale;
+    a.sigma2 = theta->sigma2;
+    a.pc = &pc;
+    a.B = R;
+    a.ldb = N;
+    a.t = t;
+    a.tol = inner_tol;
+    a.max_iter = max_iter;
+    a.precision = inner_precision;
+    a.U = Dl;
+    a.ldu = N;
+    a.alpha_hist = ah;
+    a.beta_hist = bh;
+    a.iters_dev = it_dev;
+    a.relres_dev = rr_dev;
+    CgResult res;
+    GP_TRY(mbcg_run(ctx, a, &res));
+    // an inner breakdown (the inner operator lost definiteness) leaves the
+    // iterate reached so far in delta; it is used, and the round must then
+    // still reduce some residual
+    const bool broke = res.breakdown;
+    inner += res.iters_max;
+    ++outer;
+    // Omega += delta; R = B - K-hat Omega in the outer precision
+    GP_TRY(axpby_vectors(ctx, 1.f, Omega, 1.f, Dl, Omega, N, N, t));
+    GP_TRY(kmv(ctx, po, po, Omega, N, t, W, N, theta->outputscale, theta->sigma2, true, outer_precision));
+    GP_TRY(axpby_vectors(ctx, 1.f, B, -1.f, W, R, N, N, t));
+    GP_TRY(dot_columns(ctx, R, R, N, N, t, rr));
+    GP_CUDA(ctx, cudaMemcpyAsync(h, rr, sizeof(double) * t, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(ctx, cudaStreamSynchronize(st));
+    GP_TRY(check_status(ctx));
+    bool progress = false;
+    for (int c = 0; c < t; ++c) {
+      if (done[c]) continue;
+      const double prev = rel[c];
+      rel[c] = std::sqrt(h[c]) / bnorm[c];
+      if (rel[c] < 0.9 * prev) progress = true;
+      if (rel[c] < tol) {
+        done[c] = 1;
+        // a stopped column's residual is not refined further
+        GP_CUDA(ctx, cudaMemsetAsync(R + (size_t)c * N, 0, sizeof(float) * N, st));
+      }
+    }
+    if (broke && !progress) {
+      if (outer_steps) *outer_steps = outer;
+      if (inner_steps) *inner_steps = inner;
+      if (rel_resid) std::memcpy(rel_resid, rel.data(), sizeof(double) * t);
+      return set_err(ctx, GP_EBREAKDOWN, "refinement: inner mBCG breakdown without progress");
+    }
+  }
+  all = true;
+  for (int c = 0; c < t; ++c) all = all && done[c];
+  if (outer_steps) *outer_steps = outer;
+  if (inner_steps) *inner_steps = inner;
+  if (rel_resid) std::memcpy(rel_resid, rel.data(), sizeof(double) * t);
+  if (!all) return set_err(ctx, GP_ENOTCONV, "refinement: tol not reached after %d rounds", outer);
   return GP_OK;
 }
 

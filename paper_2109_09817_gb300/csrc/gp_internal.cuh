@@ -44,6 +44,7 @@ enum WsSlot {
   WS_LZ_SCR, WS_LZ_OUT,
   WS_GR_U, WS_GR_W, WS_GR_ACC,
   WS_PR_K, WS_PR_O, WS_STATUS, WS_PC_DG, WS_PC_DH, WS_PC_RES,
+  WS_RF_R, WS_RF_D, WS_RF_W, WS_RF_S,
   WS_COUNT
 };
 
@@ -53,6 +54,31 @@ struct DevBuf {
 };
 
 }  // namespace gp
+
+// A fitted model resident on the device (gp_model_fit / gp_predict).
+struct gp_model {
+  int device = 0;
+  int64_t n = 0, n_pad = 0;
+  int d = 0, d_pad = 0;
+  int precision = GP_FP32_PLAIN;
+  std::vector<double> ell;
+  double s = 1.0, sigma2 = 1e-4, tol = 1e-6;
+  int max_iter = 1000;
+  double* mu = nullptr;
+  float* xt = nullptr;
+  float* norm = nullptr;
+  float* xt_hi = nullptr;
+  float* xt_lo = nullptr;
+  __nv_bfloat16* xb_hi = nullptr;
+  __nv_bfloat16* xb_lo = nullptr;
+  float* alpha = nullptr;      // n_pad, zero padded
+  double* L = nullptr;         // n x k
+  int k = 0;
+  float* L32 = nullptr;
+  double* cfac = nullptr;
+  float* dh = nullptr;         // D^{-1/2}, n_pad
+  double pc_logdet = 0.0;
+};
 
 struct gp_ctx {
   int device = 0;
@@ -223,5 +249,9 @@ int probe_vectors(gp_ctx* ctx, const double* L, int64_t n, int k, double sigma2,
                   const double* resid, uint64_t seed, int n_probes, float* Z, int64_t ldz);
 int copy_vectors(gp_ctx* ctx, const float* src, int64_t lds, float* dst,
                  int64_t ldd, int64_t n, int t, float scale);
+// out = a X + b Y for t vectors of length n (common leading dimension ld);
+// out may alias X or Y
+int axpby_vectors(gp_ctx* ctx, float a, const float* X, float b, const float* Y, float* out,
+                  int64_t ld, int64_t n, int t);
 
 }  // namespace gp

@@ -110,23 +110,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-// The same with compile-time byte/16 offsets added to the SMEM descriptors
-// (and to the TMEM A address) inside the asm, so that the offsets stay
-// immediates instead of registers held across the tile loop.
+// tcgen05.mma kind::tf32 (A from SMEM: _ss, from TMEM: _ts) with compile-time
+// byte/16 offsets added to the SMEM descriptors (and to the TMEM A address)
+// inside the asm, so that the offsets stay immediates instead of registers
+// held across the tile loop.
 template <uint32_t AO, uint32_t BO>
 __device__ __forceinline__ void mma_ss_imm(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -164,11 +151,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                  "=r"(r[7])
-               : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
@@ -678,6 +660,13 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   const int64_t col_tiles = ceil_div(cols.n, BN);
   int64_t splits = std::max<int64_t>(1, ceil_div(4LL * ctx->num_sms, row_tiles));
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, col_tiles / 4));
+  // Column bands that fit in L2: blockIdx.x (row tiles) varies fastest in
+  // launch order, so every row tile finishes band y before band y + 1 starts
+  // and each band of X~_J / V_J is read from DRAM about once, instead of once
+  // per wave of CTAs that have drifted apart.
+  const int64_t tile_bytes = (int64_t)BN * (DP + T) * 4 * (SPLIT ? 2 : 1) + 256;
+  const int64_t band_tiles = std::max<int64_t>(64, (48LL << 20) / tile_bytes);
+  splits = std::max<int64_t>(splits, ceil_div(col_tiles, band_tiles));
   const int64_t per = ceil_div(col_tiles, splits);
   splits = ceil_div(col_tiles, per);
   TcParams prm;
