@@ -8,7 +8,9 @@
 //                                  split: S = hi.hi^T + hi.lo^T + lo.hi^T
 //   epi   K = matern(n_a + n_b - 2S) on the FP32/MUFU pipes (8 warps), written
 //         back to TMEM as K_hi (over S) and K_lo = tf32(K - K_hi)
-//   MMA2  O_J = K_hi V_hi + K_hi V_lo + K_lo V_hi    (A operand from TMEM)
+//   MMA2  O_J = K_hi [V_hi V_lo] (kind::tf32) + K_lo V_hi (kind::f16, BF16
+//         operands: K_lo is 2^-11 of K, so BF16 keeps the term to 2^-20 of
+//         K V and covers 16 columns per MMA instead of 8); A from TMEM
 //   epi   O_J drained from TMEM and added into per-thread registers with a
 //         compensated (Kahan) sum; flushed once per CTA with atomics.
 // The tensor pipe loses roughly 500 cycles whenever it drains, so MMA1 runs
@@ -106,6 +108,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// Instruction descriptor: kind::f16 with BF16 A and B, D = F32, K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 // Instruction descriptor: kind::tf32, D = F32, A and B K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -132,6 +138,16 @@ __device__ __forceinline__ void mma_ts_imm(uint32_t d, uint32_t a_tmem, uint64_t
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc), "n"(AO), "n"(BO)
       : "memory");
 }
+template <uint32_t AO, uint32_t BO>
+__device__ __forceinline__ void mma_ts_bf16_imm(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                                uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b32 ta;\n .reg .b64 db;\n add.u32 ta, %1, %5;\n add.s64 db, %2, %6;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [ta], db, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc), "n"(AO), "n"(BO)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
@@ -152,6 +168,11 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                  "=r"(r[7])
                : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
 }
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
@@ -214,9 +235,11 @@ struct TcLayout {
   // hi and lo stack into one N = 128 B operand
   static constexpr int X_SLOT = KB * 2 * XJ_BOX;
   static constexpr int X0 = A_LO + KB * A_BOX;
-  // V_J slot: per 32-column box vb: [hi T rows][lo T rows], then the 64
+  // V_J slot: per 32-column box vb: [hi T rows][lo T rows]; then V_hi in
+  // BF16 (T rows of 64 columns = one 128-byte atom row each); then the 64
   // column norms
-  static constexpr int V_NRM = 2 * 2 * V_BOX;
+  static constexpr int V_BF = 2 * 2 * V_BOX;
+  static constexpr int V_NRM = V_BF + T * 128;
   static constexpr int V_SLOT = (V_NRM + 256 + 1023) / 1024 * 1024;
   static constexpr int V0 = X0 + XS * X_SLOT;
   static constexpr int BAR = V0 + VS * V_SLOT;
@@ -224,7 +247,8 @@ struct TcLayout {
   static constexpr int TOTAL = BAR + NBAR * 8 + 16;
   static constexpr uint32_t TX_A = 2u * KB * A_BOX;
   static constexpr uint32_t TX_X = 2u * KB * XJ_BOX;
-  static constexpr uint32_t TX_V = 4u * V_BOX + 256u;
+  static constexpr uint32_t TX_V = 4u * V_BOX + T * 128u + 256u;   // split form
+  static constexpr uint32_t TX_V1 = 2u * V_BOX + 256u;             // single TF32
   // TMEM columns
   // per S buffer b: [b*128, +64) the hi.hi product, then K_hi;
   //                 [b*128+64, +64) the hi.lo + lo.hi products, then K_lo
@@ -274,11 +298,21 @@ __device__ __forceinline__ void mma2_steps(uint32_t d, uint32_t khi, uint32_t kl
     const uint32_t acc = KK == 0 ? acc0 : 1u;
     if constexpr (SPLIT) {
       mma_ts_imm<KK * 8, BO>(d, khi, dV, id2w, acc);
-      mma_ts_imm<KK * 8, BO>(d, klo, dV, id2, 1u);
     } else {
       mma_ts_imm<KK * 8, BO>(d, khi, dV, id2, acc);
     }
     mma2_steps<Ly, SPLIT, KK + 1, NK>(d, khi, klo, dV, id2w, id2, acc0);
+  }
+}
+// K_lo V_hi in BF16, 16 columns per k-step.  The epilogue packs K_lo of
+// columns [32h, 32h + 32) into TMEM columns [32h, 32h + 16) of the S_x
+// region, two BF16 per 32-bit column, so k-step kk reads 8 columns at
+// (kk >> 1) * 32 + (kk & 1) * 8; B = V_hi (BF16), 32 bytes per k-step.
+template <class Ly, int KK, int NK>
+__device__ __forceinline__ void mma2_lo_steps(uint32_t d, uint32_t klo, uint64_t dVb, uint32_t id) {
+  if constexpr (KK < NK) {
+    mma_ts_bf16_imm<(KK >> 1) * 32 + (KK & 1) * 8, ((KK * 32) >> 4)>(d, klo, dVb, id, 1u);
+    mma2_lo_steps<Ly, KK + 1, NK>(d, klo, dVb, id);
   }
 }
 
@@ -288,7 +322,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constant__ CUtensorMap map_r_lo,
               const __grid_constant__ CUtensorMap map_c_hi, const __grid_constant__ CUtensorMap map_c_lo,
               const __grid_constant__ CUtensorMap map_v_hi, const __grid_constant__ CUtensorMap map_v_lo,
-              const TcParams p) {
+              const __grid_constant__ CUtensorMap map_v_bf, const TcParams p) {
   using Ly = TcLayout<DP, T>;
   constexpr int NSB = Ly::NSB, XS = Ly::XS, VS = Ly::VS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -376,11 +410,12 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
         break;
       }
       uint8_t* vb = smem + Ly::V0 + vs * Ly::V_SLOT;
-      mbar_expect_tx(bar_vf + vs, SPLIT ? Ly::TX_V : Ly::TX_V - 2u * Ly::V_BOX);
+      mbar_expect_tx(bar_vf + vs, SPLIT ? Ly::TX_V : Ly::TX_V1);
       for (int b = 0; b < 2; ++b) {
         tma_2d(vb + (2 * b) * Ly::V_BOX, &map_v_hi, bar_vf + vs, col0 + b * 32, 0);
         if (SPLIT) tma_2d(vb + (2 * b + 1) * Ly::V_BOX, &map_v_lo, bar_vf + vs, col0 + b * 32, 0);
       }
+      if (SPLIT) tma_2d(vb + Ly::V_BF, &map_v_bf, bar_vf + vs, col0, 0);
       bulk_g2s(vb + Ly::V_NRM, p.nc + col0, 256, bar_vf + vs);
       armed = j + 1;
     }
@@ -400,6 +435,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
     constexpr uint32_t ID1W = idesc_tf32(BM, 2 * BN);     // N = 128: [hi; lo] stacked
     constexpr uint32_t ID2 = idesc_tf32(BM, T);
     constexpr uint32_t ID2W = idesc_tf32(BM, 2 * T);
+    constexpr uint32_t ID2B = idesc_bf16(BM, T);
     // SMEM descriptors are built once; an operand at byte offset o from a
     // 1024-aligned base has descriptor desc(base) + (o >> 4), so every MMA
     // below issues with constant offsets (a single issuing thread would
@@ -435,6 +471,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       const uint32_t d = tbase + ocol;
       const uint32_t khi = tbase + Ly::T_S + b * 128, klo = khi + Ly::T_X;
       mma2_steps<Ly, SPLIT, 0, BN / 8>(d, khi, klo, dV, ID2W, ID2, first ? 0u : 1u);
+      if constexpr (SPLIT) mma2_lo_steps<Ly, 0, BN / 16>(d, klo, dV + (Ly::V_BF >> 4), ID2B);
       return true;
     };
     if (warp == 1) {
@@ -541,8 +578,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
           // u = u2 / sqrt(u2) with one MUFU op; the floor keeps u2 = 0 at 0
           const float uu = u2 * rsqrt_approx(fmaxf(u2, 1e-30f));
           const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
-          // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder
-          // (|lo| <= 2^-11 |K|, so kind::tf32 reading lo costs <= 2^-22 |K|)
+          // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder;
+          // |lo| <= 2^-11 |K|, so lo rounded to BF16 costs <= 2^-20 |K|
           const float hi = tf32_rna(kv);
           sh[c] = __float_as_uint(hi);
           sx[c] = __float_as_uint(kv - hi);
@@ -559,7 +596,18 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
           }
         }
         tmem_st16(sa, sh);
-        if (SPLIT) tmem_st16(sa + Ly::T_X, sx);
+        if (SPLIT) {
+          // K_lo as BF16 pairs (even column in the low half) into this warp's
+          // own S_x columns, already read above: [32h + 8 half, +8)
+          uint32_t lo2[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 v =
+                __floats2bfloat162_rn(__uint_as_float(sx[2 * i]), __uint_as_float(sx[2 * i + 1]));
+            lo2[i] = *reinterpret_cast<const uint32_t*>(&v);
+          }
+          tmem_st8(tbase + lane_off + Ly::T_S + b * 128 + Ly::T_X + h * 32 + half * 8, lo2);
+        }
       }
       tmem_wait_st();
       fence_before();
@@ -592,7 +640,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
 // length n_pad (zero padding).
 __global__ void split_v_kernel(const float* __restrict__ V, int64_t ldv, int t, int64_t n,
                                int tpad, int64_t npad, float* __restrict__ vhi,
-                               float* __restrict__ vlo) {
+                               float* __restrict__ vlo, __nv_bfloat16* __restrict__ vbf) {
   const int64_t total = (int64_t)tpad * npad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -601,6 +649,7 @@ __global__ void split_v_kernel(const float* __restrict__ V, int64_t ldv, int t, 
     const float h = tf32_rna(v);
     vhi[i] = h;
     vlo[i] = tf32_rna(v - h);
+    if (vbf) vbf[i] = __float2bfloat16_rn(h);
   }
 }
 
@@ -620,15 +669,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2D FP32 tensor [rows][cols] (cols contiguous), box = 32 cols x box_rows,
 // 128-byte swizzle.
-int make_map(gp_ctx* ctx, CUtensorMap* m, const float* base, int64_t rows, int64_t cols,
-             int64_t ld, int box_rows, int box_cols = 32, bool swizzle = true) {
+int make_map(gp_ctx* ctx, CUtensorMap* m, const void* base, int64_t rows, int64_t cols,
+             int64_t ld, int box_rows, int box_cols = 32, bool swizzle = true, bool bf16 = false) {
   auto fn = encode_fn();
   if (!fn) return set_err(ctx, GP_ECUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t gstr[1] = {(cuuint64_t)ld * sizeof(float)};
+  const size_t es_bytes = bf16 ? 2 : 4;
+  cuuint64_t gstr[1] = {(cuuint64_t)ld * es_bytes};
   cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1u, 1u};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstr, box, es,
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(base), gdim, gstr, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE,
                   swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -638,9 +689,10 @@ int make_map(gp_ctx* ctx, CUtensorMap* m, const float* base, int64_t rows, int64
 
 template <int DP, int T, bool SPLIT>
 int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi, const float* vlo,
-              int64_t vld, int t, float* out, int64_t ldo, float s, bool sym, bool split, int* status) {
+              const __nv_bfloat16* vbf, int64_t vld, int t, float* out, int64_t ldo, float s, bool sym,
+              bool split, int* status) {
   using Ly = TcLayout<DP, T>;
-  CUtensorMap mrh, mrl, mch, mcl, mvh, mvl;
+  CUtensorMap mrh, mrl, mch, mcl, mvh, mvl, mvb;
   const float* rlo = split ? rows.xt_lo : rows.xt_hi;
   const float* clo = split ? cols.xt_lo : cols.xt_hi;
   GP_TRY(make_map(ctx, &mrh, rows.xt_hi, rows.n_pad, DP, DP, BM));
@@ -649,6 +701,12 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   GP_TRY(make_map(ctx, &mcl, clo, cols.n_pad, DP, DP, BN));
   GP_TRY(make_map(ctx, &mvh, vhi, T, cols.n_pad, vld, T));
   GP_TRY(make_map(ctx, &mvl, split ? vlo : vhi, T, cols.n_pad, vld, T));
+  // V_hi in BF16: boxes of 64 columns (128 bytes) x T rows
+  if (split) {
+    GP_TRY(make_map(ctx, &mvb, vbf, T, cols.n_pad, vld, T, 64, true, true));
+  } else {
+    mvb = mvh;
+  }
   const size_t smem = Ly::TOTAL + 1024;
   static bool attr = false;
   if (!attr) {
@@ -682,7 +740,7 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   prm.tiles_per_split = (int)per;
   prm.status = status;
   kmv_tc_kernel<DP, T, SPLIT><<<dim3((unsigned)row_tiles, (unsigned)splits), NTHREADS, smem, ctx->stream>>>(
-      mrh, mrl, mch, mcl, mvh, mvl, prm);
+      mrh, mrl, mch, mcl, mvh, mvl, mvb, prm);
   GP_LAUNCHED(ctx);
   return GP_OK;
 }
@@ -735,27 +793,28 @@ int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V, int6
     const int T = tc <= 16 ? 16 : 32;
     float* vhi = ws<float>(ctx, WS_VHI, (size_t)T * npad);
     float* vlo = ws<float>(ctx, WS_VLO, (size_t)T * npad);
-    if (!vhi || !vlo) return set_err(ctx, GP_ENOMEM, "workspace (V split)");
+    __nv_bfloat16* vbf = split ? ws<__nv_bfloat16>(ctx, WS_VBHI, (size_t)T * npad) : nullptr;
+    if (!vhi || !vlo || (split && !vbf)) return set_err(ctx, GP_ENOMEM, "workspace (V split)");
     const int64_t total = (int64_t)T * npad;
     const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 16LL * ctx->num_sms);
-    split_v_kernel<<<g, 256, 0, ctx->stream>>>(V + (int64_t)c0 * ldv, ldv, tc, cols.n, T, npad, vhi, vlo);
+    split_v_kernel<<<g, 256, 0, ctx->stream>>>(V + (int64_t)c0 * ldv, ldv, tc, cols.n, T, npad, vhi, vlo, vbf);
     GP_LAUNCHED(ctx);
     float* oc = out + (int64_t)c0 * ldo;
     int rc;
     if (split) {
       if (rows.d_pad == 32)
-        rc = T == 16 ? launch_tc<32, 16, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status)
-                     : launch_tc<32, 32, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status);
+        rc = T == 16 ? launch_tc<32, 16, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status)
+                     : launch_tc<32, 32, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status);
       else
-        rc = T == 16 ? launch_tc<64, 16, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status)
-                     : launch_tc<64, 32, true>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, true, status);
+        rc = T == 16 ? launch_tc<64, 16, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status)
+                     : launch_tc<64, 32, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status);
     } else {
       if (rows.d_pad == 32)
-        rc = T == 16 ? launch_tc<32, 16, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status)
-                     : launch_tc<32, 32, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status);
+        rc = T == 16 ? launch_tc<32, 16, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status)
+                     : launch_tc<32, 32, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status);
       else
-        rc = T == 16 ? launch_tc<64, 16, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status)
-                     : launch_tc<64, 32, false>(ctx, rows, cols, vhi, vlo, npad, tc, oc, ldo, s, sym, false, status);
+        rc = T == 16 ? launch_tc<64, 16, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status)
+                     : launch_tc<64, 32, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status);
     }
     if (rc != GP_OK) return rc;
   }
