@@ -24,6 +24,9 @@ int set_err(gp_ctx* ctx, int code, const char* fmt, ...) {
 }
 
 int check_cuda(gp_ctx* ctx, cudaError_t e, const char* what) {
+  // clear a non-sticky error so that it is not reported again by the next
+  // launch check (a sticky one stays, and every later call reports it)
+  cudaGetLastError();
   if (e == cudaErrorMemoryAllocation)
     return set_err(ctx, GP_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
   return set_err(ctx, GP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -497,7 +500,7 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
     GP_CUDA(ctx, cudaMemsetAsync(Wg, 0, sizeof(float) * ld * T1, ctx->stream));
     GP_TRY(copy_vectors(ctx, U, ld, Wg, ld, N, 1, 0.5f));
     GP_TRY(copy_vectors(ctx, Z0 + ld, ld, Wg + ld, ld, N, n_probes, (float)(-0.5 / n_probes)));
-    GP_TRY(grad_tiles(ctx, p, U, Wg, T1, Gacc, nullptr));
+    GP_TRY(grad_tiles(ctx, p, U, Wg, T1, Gacc, nullptr, precision));
     GP_TRY(dot_columns(ctx, U, Wg, ld, N, T1, dots + 1));
   }
   // 7. host assembly

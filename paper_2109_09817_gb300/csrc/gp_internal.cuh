@@ -44,7 +44,7 @@ enum WsSlot {
   WS_LZ_SCR, WS_LZ_OUT,
   WS_GR_U, WS_GR_W, WS_GR_ACC,
   WS_PR_K, WS_PR_O, WS_STATUS, WS_PC_DG, WS_PC_DH, WS_PC_RES,
-  WS_RF_R, WS_RF_D, WS_RF_W, WS_RF_S,
+  WS_RF_R, WS_RF_D, WS_RF_W, WS_RF_S, WS_GT_P, WS_GT_T,
   WS_COUNT
 };
 
@@ -238,8 +238,12 @@ int lanczos_quadrature(gp_ctx* ctx, const double* alpha_hist,
 // ---- gradient -----------------------------------------------------------------
 // G[j] (d_pad doubles) and gs (1 double) accumulated by the backward kernel
 // for M_sym = 1/2 (U W^T + W U^T), U, W: T1 vectors of length n (ld n_pad).
+// precision GP_FP32_SPLIT_TF32 with d_pad 32/64 and 2 T1 <= 64 runs the
+// tensor-core backward (grad_tc.cu), otherwise the CUDA-core one.
 int grad_tiles(gp_ctx* ctx, const Prep& p, const float* U, const float* W,
-               int T1, double* G, double* gs);
+               int T1, double* G, double* gs, int precision);
+bool grad_tc_supported(const Prep& p, int T1);
+int grad_tc(gp_ctx* ctx, const Prep& p, const float* U, const float* W, int T1, double* G);
 
 // ---- small helpers (cg.cu) ------------------------------------------------------
 // out[c] = sum_a A[c*ld + a] * B[c*ld + a] in FP64, c < t (device doubles)

@@ -130,3 +130,42 @@ def test_tc_logml_and_predict(gp, ctx):
     mr, _ = go.predict(w.X, w.y.astype(np.float64), w.Xtest, w.lengthscale, 1.0, w.sigma2)
     assert np.linalg.norm(mean.cpu().numpy() - mr) <= 1e-4 * np.linalg.norm(mr)
     m.free()
+
+
+def test_tc_full_size_solve_gp256k(gp, ctx):
+    """A solve at full size in the benchmark's configuration (split TF32,
+    rank-64 residual-diagonal preconditioner, tol 1e-4): the true relative
+    residual of the y column on 96 rows sampled by the oracle (an estimate of
+    the full ratio, gated at 2e-4)."""
+    w = make_workload("gp256k")
+    X = torch.from_numpy(w.X).cuda()
+    th = gp.Theta(w.lengthscale, 1.0, w.sigma2)
+    L, _, _, res_d = gp.gp_pivchol(ctx, X, th, 64, want_resid=True)
+    B = w.y[None, :].astype(np.float32)
+    r = gp.gp_mbcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=1e-4, max_iter=400,
+                   precision=gp.GP_FP32_SPLIT_TF32, resid=res_d, allow_notconv=False)
+    assert r["rc"] == 0
+    Om = r["Omega"].cpu().numpy().T.astype(np.float64)
+    rows = np.sort(np.random.default_rng(8).choice(w.N, size=96, replace=False))
+    res = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T, rows)
+    assert res.max() <= 2e-4, res
+
+
+@pytest.mark.parametrize("name,N,d", [("gp2k", 1500, 32), ("gp256k", 1024, 64)])
+def test_tc_backward_matches_oracle(gp, ctx, name, N, d):
+    """Tensor-core backward (split TF32, d_pad 32 and 64) against the
+    oracle's same-probe gradient; the solve runs in split TF32 as well."""
+    w = make_workload(name, N=N, d=d)
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(w.y).cuda()
+    th = gp.Theta(w.lengthscale, 1.0, w.sigma2)
+    seed, k, npr = 4, 32, 15
+    r = gp.gp_logml_and_grad(ctx, X, th, y, n_probes=npr, seed=seed, k=k, tol=1e-6,
+                             max_iter=2000, precision=gp.GP_FP32_SPLIT_TF32,
+                             allow_notconv=True, precond=gp.GP_PC_RESID)
+    L, pr, _ = go.pivoted_cholesky(w.X, w.lengthscale, 1.0, k)
+    rr = go.residual_diagonal(w.X, w.lengthscale, 1.0, L, pr)
+    Zp = go.probe_vectors(L, w.sigma2, seed, npr, rr)
+    g_ref = go.same_probe_grad(w.X, w.y.astype(np.float64), w.lengthscale, 1.0, w.sigma2, Zp,
+                               go.precond_solve(L, w.sigma2, Zp, rr))
+    assert np.abs(r["grad"] - g_ref).max() <= 1e-3 * np.abs(g_ref).max()
