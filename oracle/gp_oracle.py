@@ -48,6 +48,7 @@ __all__ = [
     "mbcg", "lanczos_tridiagonal", "quadrature_log", "slq_logdet",
     "same_probe_logdet_target", "dkhat_dtheta", "exact_grad",
     "same_probe_grad", "predict", "true_relative_residual",
+    "sym_precond_factor", "sym_precond_apply", "bcg",
 ]
 
 
@@ -299,6 +300,77 @@ def mbcg(matmul, B, psolve, tol, max_iter):
             rz[c] = rz_new[c]
     return dict(U=U, alpha=alphas, beta=betas, iters=iters, relres=relres,
                 rz0=rz0)
+
+
+# ----------------------------------------------------------------------------
+# AltBBMM (Sec. 3.2): block CG (BCG, Sec. 3.1) with symmetric preconditioning
+# S^T K-hat S, S S^T = P^{-1}, and the Nystrom preconditioner.  Reading: the
+# Nystrom landmarks are the greedy pivoted-Cholesky pivots, so the low-rank
+# part of P is the same L L^T as in BBMM; P = L L^T + D as above.
+# ----------------------------------------------------------------------------
+def sym_precond_factor(L, sigma2, resid=None):
+    """Factors of S = D^{-1/2} (I + Lt Lt^T)^{-1/2} with Lt = D^{-1/2} L, so
+    that S S^T = P^{-1}.  With Lt^T Lt = V diag(lam) V^T,
+    (I + Lt Lt^T)^{-1/2} = I + Lt Cp Lt^T, Cp = V diag(g(lam)) V^T,
+    g(lam) = ((1 + lam)^{-1/2} - 1) / lam = -1 / (sqrt(1+lam) (1 + sqrt(1+lam))).
+    Returns (dh = D^{-1/2}, Lt, Cp)."""
+    L = np.asarray(L, F64)
+    dh = 1.0 / np.sqrt(precond_diag(L, sigma2, resid))
+    Lt = dh[:, None] * L
+    lam, V = np.linalg.eigh(Lt.T @ Lt)
+    lam = np.maximum(lam, 0.0)
+    r = np.sqrt(1.0 + lam)
+    g = -1.0 / (r * (1.0 + r))
+    return dh, Lt, (V * g) @ V.T
+
+
+def sym_precond_apply(fac, V, transpose=False):
+    """S V (transpose=False: dh o (G V)) or S^T V (G (dh o V)), with
+    G = I + Lt Cp Lt^T symmetric."""
+    dh, Lt, Cp = fac
+    V = np.asarray(V, F64)
+    dv = dh[:, None] if V.ndim == 2 else dh
+    if transpose:
+        V = dv * V
+    GV = V + Lt @ (Cp @ (Lt.T @ V))
+    return GV if transpose else dv * GV
+
+
+def bcg(matmul, B, fac, tol, max_iter):
+    """Block CG (O'Leary's recurrences) on A = S^T K-hat S, right-hand sides
+    S^T B; Omega = S W solves K-hat Omega = B for all s columns together.
+
+    Per step: Dt = S D, W = K-hat Dt, Q = S^T W, alpha = (D^T Q)^{-1} (Rh^T Rh),
+    Omega += Dt alpha, R -= W alpha, Rh -= Q alpha,
+    beta = (Rh^T Rh)^{-1} (Rh'^T Rh'), D = Rh' + D beta.
+    R = B - K-hat Omega is carried by its recurrence; the solve stops when all
+    s relative residuals ||R_c|| / ||B_c|| are below tol (Sec. 4) or after
+    max_iter steps.  Returns dict(Omega, iters, relres)."""
+    B = np.asarray(B, F64)
+    N, s = B.shape
+    Om = np.zeros_like(B)
+    R = B.copy()
+    Rh = sym_precond_apply(fac, R, transpose=True)
+    D = Rh.copy()
+    rho = Rh.T @ Rh
+    bnorm = np.linalg.norm(B, axis=0)
+    relres = np.ones(s)
+    it = 0
+    while it < max_iter and np.any(relres >= tol):
+        Dt = sym_precond_apply(fac, D)
+        W = matmul(Dt)
+        Q = sym_precond_apply(fac, W, transpose=True)
+        alpha = np.linalg.solve(D.T @ Q, rho)
+        Om += Dt @ alpha
+        R -= W @ alpha
+        Rh -= Q @ alpha
+        rho_new = Rh.T @ Rh
+        beta = np.linalg.solve(rho, rho_new)
+        D = Rh + D @ beta
+        rho = rho_new
+        relres = np.linalg.norm(R, axis=0) / bnorm
+        it += 1
+    return dict(Omega=Om, iters=it, relres=relres)
 
 
 def lanczos_tridiagonal(alpha, beta, m=None):
