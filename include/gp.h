@@ -178,6 +178,24 @@ GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
             double* alpha_hist, double* beta_hist, int* iters,
             double* rel_resid);
 
+/* AltBBMM solve (Sec. 3.2): block CG (Sec. 3.1, BCG) on the symmetrically
+ * preconditioned system S^T K-hat S W = S^T B, Omega = S W, with S S^T =
+ * P^{-1}, P = L L^T + D the Nystrom preconditioner whose landmarks are the
+ * pivots of gp_pivchol (L, rank k; D = sigma^2 I, or diag(resid_diag) +
+ * sigma^2 I when resid_diag is given; k = 0: S = D^{-1/2}).  All t columns
+ * share one block Krylov space; the solve stops when every relative residual
+ * ||B_c - K-hat Omega_c|| / ||B_c|| (by its recurrence) is below tol.
+ * B, Omega: device, N x t column-major (ld N), 1 <= t <= 32, no zero column
+ * (GP_EINVAL).  iters (host int, nullable): block steps taken; rel_resid
+ * (host t doubles, nullable).  GP_ENOTCONV after max_iter steps (Omega holds
+ * the last iterate); GP_EBREAKDOWN if a block Gram matrix loses definiteness.
+ * Synchronises every step. */
+GP_API int gp_bcg(gp_ctx* ctx, const float* X, int64_t N, int d,
+                  const gp_theta* theta, const double* L, int k,
+                  const double* resid_diag, const float* B, int t, double tol,
+                  int max_iter, int precision, float* Omega, int* iters,
+                  double* rel_resid);
+
 /* Mixed-precision iterative refinement of K-hat Omega = B (the solve of
  * Sec. 3.1; the refinement loop itself is not in the paper).  Starting from
  * Omega = 0: solve K-hat delta = R with preconditioned mBCG whose products use

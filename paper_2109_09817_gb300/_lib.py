@@ -18,7 +18,7 @@ GP_PC_SIGMA, GP_PC_RESID = 0, 1
 EXPORTS = (
     "gp_create", "gp_destroy", "gp_set_stream", "gp_sync", "gp_last_error",
     "gp_launch_count", "gp_profile", "gp_profile_read", "gp_kmatmul", "gp_kcross_matmul", "gp_pivchol", "gp_mbcg",
-    "gp_mbcg_refine", "gp_logml_and_grad", "gp_model_fit", "gp_model_free", "gp_predict",
+    "gp_mbcg_refine", "gp_bcg", "gp_logml_and_grad", "gp_model_fit", "gp_model_free", "gp_predict",
     "gp_kmatmul_noalloc", "gp_server_create", "gp_server_add_model", "gp_server_predict",
     "gp_server_solve", "gp_server_wait", "gp_server_stats", "gp_server_last_error",
     "gp_server_destroy",
@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
         "gp_pivchol": (c_int, [vp, vp, i64, c_int, th, c_int, vp, vp, ip, vp]),
         "gp_mbcg": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, vp, c_int, c_dbl, c_int,
                             c_int, vp, vp, vp, ip, dp]),
+        "gp_bcg": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, vp, c_int, c_dbl, c_int, c_int,
+                           vp, ip, dp]),
         "gp_mbcg_refine": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, vp, c_int, c_dbl,
                                    c_dbl, c_int, c_int, c_int, c_int, vp, ip, ip, dp]),
         "gp_logml_and_grad": (c_int, [vp, vp, i64, c_int, th, vp, c_int, ctypes.c_uint64,

@@ -186,6 +186,31 @@ def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tenso
                 relres=np.array(rr[:]), rc=rc)
 
 
+def gp_bcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tensor],
+           B: torch.Tensor, tol: float = 1e-4, max_iter: int = 1000,
+           precision: int = GP_FP32_SPLIT_TF32, resid: Optional[torch.Tensor] = None,
+           allow_notconv: bool = False):
+    """AltBBMM block CG on S^T K-hat S (t <= 32 right-hand sides); returns
+    dict(Omega, iters, relres, rc)."""
+    _dev(ctx, X, torch.float32, "X")
+    N, d = X.shape
+    B = _block(ctx, B, N, "B")
+    t = B.shape[0]
+    k = 0 if L is None else L.shape[0]
+    if L is not None:
+        _dev(ctx, L, torch.float64, "L")
+    if resid is not None:
+        _dev(ctx, resid, torch.float64, "resid")
+    Om = torch.empty_like(B)
+    it = ctypes.c_int(0)
+    rr = (ctypes.c_double * t)()
+    th, keep = theta.as_c()
+    allow = (GP_ENOTCONV,) if allow_notconv else ()
+    rc = ctx.check(ctx.lib.gp_bcg(ctx.h, _p(X), N, d, ctypes.byref(th), _p(L), k, _p(resid), _p(B), t,
+                                  tol, max_iter, precision, _p(Om), ctypes.byref(it), rr), allow=allow)
+    return dict(Omega=Om, iters=it.value, relres=np.array(rr[:]), rc=rc)
+
+
 def gp_mbcg_refine(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tensor],
                    B: torch.Tensor, tol: float = 1e-4, inner_tol: float = 1e-2,
                    max_outer: int = 10, max_iter: int = 1000,

@@ -1,0 +1,443 @@
+// AltBBMM solve: block CG on the symmetrically preconditioned system.
+//
+// arXiv 2109.09817 Sec. 3.1 (BCG: s right-hand sides share one block Krylov
+// space) and Sec. 3.2 (AltBBMM: BCG with the symmetric preconditioning
+// S^T K-hat S and a Nystrom preconditioner).  The Nystrom landmarks are the
+// greedy pivoted-Cholesky pivots, so P = L L^T + D with the factor of
+// gp_pivchol, and S = D^{-1/2} G with G = (I + Lt Lt^T)^{-1/2} = I + Lt Cp Lt^T,
+// Lt = D^{-1/2} L, Cp = V diag(g(lam)) V^T from Lt^T Lt = V diag(lam) V^T,
+// g(lam) = -1 / (sqrt(1+lam) (1 + sqrt(1+lam))).  S S^T = P^{-1}.
+//
+// Per step (O'Leary's recurrences; s x s algebra in FP64 on the host):
+//   Dt = S D,  W = K-hat Dt (fused tensor-core product),  Q = S^T W,
+//   alpha = (D^T Q)^{-1} (Rh^T Rh),  Omega += Dt alpha,  R -= W alpha,
+//   Rh -= Q alpha,  beta = (Rh^T Rh)^{-1} (Rh'^T Rh'),  D = Rh' + D beta.
+// R = B - K-hat Omega is carried by its recurrence; the solve stops when all
+// s relative residuals are below tol (Sec. 4).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gp_internal.cuh"
+
+namespace gp {
+namespace {
+
+constexpr int kGramBlocks = 512;
+
+// The factor S has condition number sqrt(kappa(P)) (~3e3 for sigma^2 = 1e-4
+// and a dominant Nystrom part), so its applications run in FP64 from the FP64
+// pivoted-Cholesky factor: Lt[i][a] = dh[a] L[i][a], dh = D^{-1/2} in FP64;
+// only the stored vectors are FP32.
+//
+// g[i][c] partial over a row chunk: sum_a Lt[i][a] (in_scale[a]) V[c][a]
+// grid (blocks, k): one pivot row i per blockIdx.y, 256 threads stride rows.
+__global__ void bcg_ltr_kernel(const double* __restrict__ L, int64_t ldl, const double* __restrict__ dh,
+                               int scale_in, const float* __restrict__ V, int64_t ldv, int64_t n, int t,
+                               double* __restrict__ part) {
+  __shared__ double red[8][32];
+  const int i = blockIdx.y;
+  const double* li = L + (int64_t)i * ldl;
+  double acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const double d = dh[a];
+    const double l = li[a] * d * (scale_in ? d : 1.0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < t) acc[c] += l * (double)V[(int64_t)c * ldv + a];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    double v = acc[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[w][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < t) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
+    part[((int64_t)blockIdx.x * gridDim.y + i) * 32 + threadIdx.x] = s;
+  }
+}
+
+// w2[i][c] = sum_j Cp[i][j] (sum_b part[b][j][c])   (k x t, FP64)
+__global__ void bcg_small_kernel(const double* __restrict__ part, int nparts, int k, int t,
+                                 const double* __restrict__ Cp, double* __restrict__ w2) {
+  extern __shared__ double g[];   // k x 32
+  for (int idx = threadIdx.x; idx < k * t; idx += blockDim.x) {
+    const int j = idx / t, c = idx % t;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[((int64_t)b * k + j) * 32 + c];
+    g[j * 32 + c] = s;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * t; idx += blockDim.x) {
+    const int i = idx / t, c = idx % t;
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += Cp[(int64_t)i * k + j] * g[j * 32 + c];
+    w2[i * 32 + c] = s;
+  }
+}
+
+// out[c][a] = post[a] * (in_scale[a] V[c][a] + sum_i Lt[i][a] w2[i][c]), FP64
+//   S V:   post = dh, in_scale = 1;   S^T V: post = 1, in_scale = dh
+__global__ void bcg_combine_kernel(const float* __restrict__ V, int64_t ldv, const double* __restrict__ L,
+                                   int64_t ldl, int k, const double* __restrict__ w2,
+                                   const double* __restrict__ dh, int transpose, int64_t n, int t,
+                                   float* __restrict__ out, int64_t ldo) {
+  extern __shared__ double sw[];   // k x 32
+  for (int idx = threadIdx.x; idx < k * 32; idx += blockDim.x) sw[idx] = w2[idx];
+  __syncthreads();
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    double lv[32];
+    const double d = dh[a];
+    for (int c = 0; c < t; ++c) lv[c] = (transpose ? d : 1.0) * (double)V[(int64_t)c * ldv + a];
+    for (int i = 0; i < k; ++i) {
+      const double l = L[(int64_t)i * ldl + a] * d;
+      for (int c = 0; c < t; ++c) lv[c] = fma(l, sw[i * 32 + c], lv[c]);
+    }
+    for (int c = 0; c < t; ++c) out[(int64_t)c * ldo + a] = (float)(transpose ? lv[c] : d * lv[c]);
+  }
+}
+
+// dh = (resid + sigma^2)^{-1/2} (or sigma^{-1}) in FP64 for rows < n
+__global__ void bcg_dh_kernel(const double* __restrict__ resid, double sigma2, int64_t n,
+                              double* __restrict__ dh) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x)
+    dh[a] = 1.0 / sqrt((resid ? resid[a] : 0.0) + sigma2);
+}
+
+// Partial t x t Gram matrices over row chunks: part[b][i][j] = sum_a A_i[a] B_j[a]
+__global__ void bcg_gram_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t ld,
+                                int64_t n, int t, double* __restrict__ part) {
+  __shared__ float sa[32][65], sb[32][65];
+  const int tid = threadIdx.x;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int npair = t * t;
+  for (int64_t a0 = (int64_t)blockIdx.x * 64; a0 < n; a0 += (int64_t)gridDim.x * 64) {
+    __syncthreads();
+    for (int idx = tid; idx < t * 64; idx += blockDim.x) {
+      const int c = idx / 64, r = idx % 64;
+      const int64_t a = a0 + r;
+      sa[c][r] = a < n ? A[(int64_t)c * ld + a] : 0.f;
+      sb[c][r] = a < n ? B[(int64_t)c * ld + a] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int pidx = tid + q * 256;
+      if (pidx < npair) {
+        const int i = pidx / t, j = pidx % t;
+        double s = 0.0;
+        for (int r = 0; r < 64; ++r) s += (double)sa[i][r] * (double)sb[j][r];
+        acc[q] += s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int pidx = tid + q * 256;
+    if (pidx < npair) part[(int64_t)blockIdx.x * 1024 + pidx] = acc[q];
+  }
+}
+
+__global__ void bcg_gram_final(const double* __restrict__ part, int nparts, int npair,
+                               double* __restrict__ out) {
+  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[(int64_t)b * 1024 + p];
+    out[p] = s;
+  }
+}
+
+// Y[c][a] = base[c][a] + sum_i X[i][a] M[i][c]   (M t x t row-major, FP32 in smem;
+// Y may alias base: each thread reads its row before writing it)
+__global__ void bcg_update_kernel(const float* __restrict__ base, const float* __restrict__ X,
+                                  const float* __restrict__ M, int64_t ld, int64_t n, int t,
+                                  float* __restrict__ Y) {
+  __shared__ float sm[32 * 32];
+  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) sm[idx] = M[idx];
+  __syncthreads();
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    float x[32], y[32];
+    for (int i = 0; i < t; ++i) x[i] = X[(int64_t)i * ld + a];
+    for (int c = 0; c < t; ++c) y[c] = base[(int64_t)c * ld + a];
+    for (int i = 0; i < t; ++i)
+      for (int c = 0; c < t; ++c) y[c] = fmaf(x[i], sm[i * t + c], y[c]);
+    for (int c = 0; c < t; ++c) Y[(int64_t)c * ld + a] = y[c];
+  }
+}
+
+// ---- host-side small linear algebra (FP64) ---------------------------------
+// Cyclic Jacobi eigenvalue iteration for a symmetric k x k matrix (row-major),
+// Golub & Van Loan Sec. 8.5: returns eigenvalues and eigenvectors (columns).
+void jacobi_eigh(std::vector<double>& A, int k, std::vector<double>& lam, std::vector<double>& V) {
+  V.assign((size_t)k * k, 0.0);
+  for (int i = 0; i < k; ++i) V[(size_t)i * k + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        const double v = A[(size_t)i * k + j] * A[(size_t)i * k + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = A[(size_t)p * k + q];
+        if (apq == 0.0) continue;
+        const double app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double tt = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + tt * tt), s = tt * c;
+        for (int r = 0; r < k; ++r) {   // A <- A J (columns p, q)
+          const double arp = A[(size_t)r * k + p], arq = A[(size_t)r * k + q];
+          A[(size_t)r * k + p] = c * arp - s * arq;
+          A[(size_t)r * k + q] = s * arp + c * arq;
+        }
+        for (int r = 0; r < k; ++r) {   // A <- J^T A (rows p, q)
+          const double apr = A[(size_t)p * k + r], aqr = A[(size_t)q * k + r];
+          A[(size_t)p * k + r] = c * apr - s * aqr;
+          A[(size_t)q * k + r] = s * apr + c * aqr;
+        }
+        for (int r = 0; r < k; ++r) {   // V <- V J
+          const double vrp = V[(size_t)r * k + p], vrq = V[(size_t)r * k + q];
+          V[(size_t)r * k + p] = c * vrp - s * vrq;
+          V[(size_t)r * k + q] = s * vrp + c * vrq;
+        }
+      }
+  }
+  lam.resize(k);
+  for (int i = 0; i < k; ++i) lam[i] = A[(size_t)i * k + i];
+}
+
+// X = A^{-1} B for SPD A (t x t) by Cholesky; false if A is not PD.
+bool spd_solve(std::vector<double> A, const std::vector<double>& B, int t, std::vector<double>& X) {
+  for (int c = 0; c < t; ++c) {
+    double dg = A[(size_t)c * t + c];
+    for (int j = 0; j < c; ++j) dg -= A[(size_t)c * t + j] * A[(size_t)c * t + j];
+    if (!(dg > 0.0)) return false;
+    dg = std::sqrt(dg);
+    A[(size_t)c * t + c] = dg;
+    for (int r = c + 1; r < t; ++r) {
+      double v = A[(size_t)r * t + c];
+      for (int j = 0; j < c; ++j) v -= A[(size_t)r * t + j] * A[(size_t)c * t + j];
+      A[(size_t)r * t + c] = v / dg;
+    }
+  }
+  X = B;
+  for (int col = 0; col < t; ++col) {
+    for (int r = 0; r < t; ++r) {   // forward
+      double v = X[(size_t)r * t + col];
+      for (int j = 0; j < r; ++j) v -= A[(size_t)r * t + j] * X[(size_t)j * t + col];
+      X[(size_t)r * t + col] = v / A[(size_t)r * t + r];
+    }
+    for (int r = t - 1; r >= 0; --r) {   // backward
+      double v = X[(size_t)r * t + col];
+      for (int j = r + 1; j < t; ++j) v -= A[(size_t)j * t + r] * X[(size_t)j * t + col];
+      X[(size_t)r * t + col] = v / A[(size_t)r * t + r];
+    }
+  }
+  return true;
+}
+
+struct SymApply {
+  const double* L = nullptr;    // FP64 pivoted-Cholesky factor, row i contiguous
+  int64_t ldl = 0;
+  const double* dh = nullptr;   // D^{-1/2}, FP64
+  int k = 0;
+  const double* Cp = nullptr;
+  double* part = nullptr;
+  double* w2 = nullptr;
+  int nparts = 0;
+};
+
+// out = S V (transpose = 0) or S^T V (transpose = 1); t <= 32 vectors, ld ld
+int sym_apply(gp_ctx* ctx, const SymApply& s, const float* V, int64_t ld, int64_t n, int t, bool transpose,
+              float* out) {
+  if (s.k == 0) {   // S = D^{-1/2}
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms);
+    bcg_combine_kernel<<<g, 256, 0, ctx->stream>>>(V, ld, s.L, s.ldl, 0, s.w2, s.dh, transpose ? 1 : 0, n, t,
+                                                   out, ld);
+    GP_LAUNCHED(ctx);
+    return GP_OK;
+  }
+  bcg_ltr_kernel<<<dim3(s.nparts, s.k), 256, 0, ctx->stream>>>(s.L, s.ldl, s.dh, transpose ? 1 : 0, V, ld, n, t,
+                                                              s.part);
+  GP_LAUNCHED(ctx);
+  bcg_small_kernel<<<1, 256, sizeof(double) * s.k * 32, ctx->stream>>>(s.part, s.nparts, s.k, t, s.Cp, s.w2);
+  GP_LAUNCHED(ctx);
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms);
+  bcg_combine_kernel<<<g, 256, sizeof(double) * s.k * 32, ctx->stream>>>(V, ld, s.L, s.ldl, s.k, s.w2, s.dh,
+                                                                         transpose ? 1 : 0, n, t, out, ld);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+int gram(gp_ctx* ctx, const float* A, const float* B, int64_t ld, int64_t n, int t, double* part, double* out) {
+  bcg_gram_kernel<<<kGramBlocks, 256, 0, ctx->stream>>>(A, B, ld, n, t, part);
+  GP_LAUNCHED(ctx);
+  bcg_gram_final<<<1, 256, 0, ctx->stream>>>(part, kGramBlocks, t * t, out);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+int update(gp_ctx* ctx, const float* base, const float* X, const float* M, int64_t ld, int64_t n, int t,
+           float* Y) {
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms);
+  bcg_update_kernel<<<g, 256, 0, ctx->stream>>>(base, X, M, ld, n, t, Y);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+}  // namespace
+
+int bcg_run(gp_ctx* ctx, const Prep& p, double s_out, double sigma2, const Precond& pc, const float* B,
+            int64_t ldb, int t, double tol, int max_iter, int precision, float* Omega, int64_t ldo,
+            int* iters_out, double* relres_out) {
+  if (t < 1 || t > 32) return set_err(ctx, GP_EINVAL, "gp_bcg: 1 <= t <= 32");
+  const int64_t n = p.n, ld = p.n_pad;
+  cudaStream_t st = ctx->stream;
+  const int k = pc.k;
+  // ---- symmetric factor: Cp from the eigenpairs of Lt^T Lt = C - I
+  SymApply sa;
+  sa.L = pc.L;
+  sa.ldl = pc.n;
+  sa.k = k;
+  sa.nparts = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 4096)), 4LL * ctx->num_sms);
+  double* Cp = ws<double>(ctx, WS_BC_C, (size_t)std::max(1, k * k));
+  double* part = ws<double>(ctx, WS_BC_P, (size_t)std::max<int64_t>(kGramBlocks * 1024, (int64_t)sa.nparts * std::max(1, k) * 32));
+  double* w2 = ws<double>(ctx, WS_BC_W, (size_t)std::max(1, k) * 32);
+  double* smalls = ws<double>(ctx, WS_BC_S, 4096);
+  double* dh64 = ws<double>(ctx, WS_BC_DH, (size_t)std::max<int64_t>(n, 1));
+  if (!Cp || !part || !w2 || !smalls || !dh64) return set_err(ctx, GP_ENOMEM, "workspace (block CG)");
+  bcg_dh_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms), 256, 0, st>>>(
+      pc.resid, sigma2, n, dh64);
+  GP_LAUNCHED(ctx);
+  sa.dh = dh64;
+  sa.Cp = Cp;
+  sa.part = part;
+  sa.w2 = w2;
+  double* h = static_cast<double*>(pinned_get(ctx, sizeof(double) * (size_t)std::max(4096, k * k)));
+  if (!h) return set_err(ctx, GP_ENOMEM, "pinned staging");
+  if (k > 0) {
+    GP_CUDA(ctx, cudaMemcpyAsync(h, pc.cfac, sizeof(double) * k * k, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<double> F(h, h + (size_t)k * k), G((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i)          // G = F F^T - I (F lower)
+      for (int j = 0; j <= i; ++j) {
+        double v = 0.0;
+        for (int q = 0; q <= j; ++q) v += F[(size_t)i * k + q] * F[(size_t)j * k + q];
+        if (i == j) v -= 1.0;
+        G[(size_t)i * k + j] = G[(size_t)j * k + i] = v;
+      }
+    std::vector<double> lam, V;
+    jacobi_eigh(G, k, lam, V);
+    std::vector<double> cp((size_t)k * k, 0.0);
+    for (int q = 0; q < k; ++q) {
+      const double r = std::sqrt(1.0 + std::max(lam[q], 0.0));
+      const double gq = -1.0 / (r * (1.0 + r));
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) cp[(size_t)i * k + j] += V[(size_t)i * k + q] * gq * V[(size_t)j * k + q];
+    }
+    std::memcpy(h, cp.data(), sizeof(double) * k * k);
+    GP_CUDA(ctx, cudaMemcpyAsync(Cp, h, sizeof(double) * k * k, cudaMemcpyHostToDevice, st));
+    GP_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  // ---- block vectors (t x ld, zero padded)
+  const size_t nv = (size_t)t * ld;
+  float* R = ws<float>(ctx, WS_BC_R, nv);
+  float* Rh = ws<float>(ctx, WS_BC_RH, nv);
+  float* D = ws<float>(ctx, WS_BC_D, nv);
+  float* D2 = ws<float>(ctx, WS_BC_D2, nv);
+  float* Dt = ws<float>(ctx, WS_BC_DT, nv);
+  float* W = ws<float>(ctx, WS_BC_WK, nv);
+  float* Q = ws<float>(ctx, WS_BC_Q, nv);
+  float* Om = ws<float>(ctx, WS_BC_OM, nv);
+  float* Mf = ws<float>(ctx, WS_BC_M, 3 * 1024);   // alpha, -alpha, beta
+  if (!R || !Rh || !D || !D2 || !Dt || !W || !Q || !Om || !Mf) return set_err(ctx, GP_ENOMEM, "workspace (block CG)");
+  for (float* v : {R, Rh, D, D2, Dt, W, Q, Om}) GP_CUDA(ctx, cudaMemsetAsync(v, 0, sizeof(float) * nv, st));
+  GP_TRY(copy_vectors(ctx, B, ldb, R, ld, n, t, 1.f));
+  GP_TRY(sym_apply(ctx, sa, R, ld, n, t, true, Rh));
+  GP_TRY(copy_vectors(ctx, Rh, ld, D, ld, n, t, 1.f));
+  double* gdev = smalls;              // t x t
+  double* rdev = smalls + 1024;       // t (column norms^2)
+  const int tt = t * t;
+  GP_TRY(gram(ctx, Rh, Rh, ld, n, t, part, gdev));
+  GP_TRY(dot_columns(ctx, B, B, ldb, n, t, rdev));
+  GP_CUDA(ctx, cudaMemcpyAsync(h, gdev, sizeof(double) * tt, cudaMemcpyDeviceToHost, st));
+  GP_CUDA(ctx, cudaMemcpyAsync(h + 1024, rdev, sizeof(double) * t, cudaMemcpyDeviceToHost, st));
+  GP_CUDA(ctx, cudaStreamSynchronize(st));
+  std::vector<double> rho(h, h + tt), bnorm(t), relres(t, 1.0);
+  for (int c = 0; c < t; ++c) {
+    bnorm[c] = std::sqrt(h[1024 + c]);
+    if (!(bnorm[c] > 0.0)) return set_err(ctx, GP_EINVAL, "gp_bcg: zero right-hand side column %d", c);
+  }
+  // matrix uploads: slot q uses its own pinned region (doubles 2048 + 512 q)
+  // and device buffer, so an upload never overwrites a region whose copy is
+  // still queued; every step synchronises before the slots are reused
+  auto put_matrix = [&](int q, const std::vector<double>& M, double scale) -> int {
+    float* hq = reinterpret_cast<float*>(h + 2048 + 512 * q);
+    for (int i = 0; i < tt; ++i) hq[i] = (float)(scale * M[i]);
+    GP_CUDA(ctx, cudaMemcpyAsync(Mf + 1024 * q, hq, sizeof(float) * tt, cudaMemcpyHostToDevice, st));
+    return GP_OK;
+  };
+  int it = 0;
+  bool conv = false;
+  while (it < max_iter) {
+    GP_TRY(sym_apply(ctx, sa, D, ld, n, t, false, Dt));
+    GP_TRY(kmv(ctx, p, p, Dt, ld, t, W, ld, s_out, sigma2, true, precision));
+    GP_TRY(sym_apply(ctx, sa, W, ld, n, t, true, Q));
+    GP_TRY(gram(ctx, D, Q, ld, n, t, part, gdev));
+    GP_CUDA(ctx, cudaMemcpyAsync(h, gdev, sizeof(double) * tt, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(ctx, cudaStreamSynchronize(st));
+    GP_TRY(check_status(ctx));
+    std::vector<double> gam(h, h + tt), alpha;
+    if (!spd_solve(gam, rho, t, alpha)) return set_err(ctx, GP_EBREAKDOWN, "gp_bcg: D^T A D not positive definite");
+    // alpha is t x t with row index = direction column, col index = rhs column
+    GP_TRY(put_matrix(0, alpha, 1.0));
+    GP_TRY(update(ctx, Om, Dt, Mf, ld, n, t, Om));
+    GP_TRY(put_matrix(1, alpha, -1.0));
+    GP_TRY(update(ctx, R, W, Mf + 1024, ld, n, t, R));
+    GP_TRY(update(ctx, Rh, Q, Mf + 1024, ld, n, t, Rh));
+    GP_TRY(gram(ctx, Rh, Rh, ld, n, t, part, gdev));
+    GP_TRY(dot_columns(ctx, R, R, ld, n, t, rdev));
+    GP_CUDA(ctx, cudaMemcpyAsync(h, gdev, sizeof(double) * tt, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(h + 1024, rdev, sizeof(double) * t, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(ctx, cudaStreamSynchronize(st));
+    ++it;
+    bool all = true;
+    for (int c = 0; c < t; ++c) {
+      relres[c] = std::sqrt(std::max(h[1024 + c], 0.0)) / bnorm[c];
+      all = all && relres[c] < tol;
+    }
+    std::vector<double> rho_new(h, h + tt);
+    if (all) {
+      conv = true;
+      break;
+    }
+    std::vector<double> beta;
+    if (!spd_solve(rho, rho_new, t, beta)) return set_err(ctx, GP_EBREAKDOWN, "gp_bcg: Rh^T Rh not positive definite");
+    GP_TRY(put_matrix(2, beta, 1.0));
+    GP_TRY(update(ctx, Rh, D, Mf + 2048, ld, n, t, D2));
+    std::swap(D, D2);
+    rho = rho_new;
+  }
+  GP_TRY(copy_vectors(ctx, Om, ld, Omega, ldo, n, t, 1.f));
+  GP_CUDA(ctx, cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = it;
+  if (relres_out) std::memcpy(relres_out, relres.data(), sizeof(double) * t);
+  if (!conv) return set_err(ctx, GP_ENOTCONV, "gp_bcg: max_iter=%d reached", max_iter);
+  return GP_OK;
+}
+
+}  // namespace gp

@@ -209,6 +209,113 @@ __global__ void z_apply_kernel(const float* __restrict__ L32, int64_t ldl, int k
   }
 }
 
+// ---- FP64 Woodbury apply ------------------------------------------------------
+// Z = P^{-1} R = dh o (dh o R - Lt w), w = C^{-1} Lt^T (dh o R), Lt = dh o L.
+// In the dominant directions of L L^T the result is (1 + lambda) times smaller
+// than dh o R, so an FP32 evaluation loses log10(1 + lambda) digits (~7 for
+// sigma^2 = 1e-4); both row passes therefore run in FP64 from the FP64 factor
+// L (row j contiguous, ld n) and dh64.
+//
+// part[(b * k + j) * t + c] = sum over rows of block b of L[j] dh^2 R_c
+// grid (blocks, k, ceil(t / 32)), 256 threads
+__global__ void ltr64_kernel(const double* __restrict__ L, int64_t ldl, int k, const float* __restrict__ R,
+                             int64_t ldr, int t, int64_t n, const CgScal* __restrict__ sc,
+                             const double* __restrict__ dh, double* __restrict__ part) {
+  __shared__ double red[8][32];
+  const int j = blockIdx.y, c0 = blockIdx.z * 32;
+  const int nc = min(32, t - c0);
+  const double* lj = L + (int64_t)j * ldl;
+  double acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  for (int64_t a = r0 + threadIdx.x; a < r1; a += blockDim.x) {
+    const double d = dh[a];
+    const double l = lj[a] * d * d;
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < nc) acc[c] += l * (double)R[(int64_t)(c0 + c) * ldr + a];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    double v = acc[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[w][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nc) {
+    double v = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
+    const int c = c0 + threadIdx.x;
+    if (sc && !sc[c].active) v = 0.0;
+    part[((int64_t)blockIdx.x * k + j) * t + c] = v;
+  }
+}
+
+// w[j][c] = sum_i Cinv[i][j] G[i][c] in FP64
+__global__ void w64_apply_kernel(const double* __restrict__ Cinv, const double* __restrict__ G, int k, int t,
+                                 double* __restrict__ w) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k * t) return;
+  const int j = idx / t, c = idx % t;
+  double s = 0.0;
+  for (int i = 0; i < k; ++i) s += Cinv[(int64_t)i * k + j] * G[(int64_t)i * t + c];
+  w[idx] = s;
+}
+
+// Z_c = dh o (dh o R_c - sum_j dh L_j w_jc) in FP64 on 32-column chunks, rz partials
+__global__ void z64_apply_kernel(const double* __restrict__ L, int64_t ldl, int k,
+                                 const double* __restrict__ w, int t, const float* __restrict__ R,
+                                 float* __restrict__ Z, int64_t ld, int64_t n, const double* __restrict__ dh,
+                                 const CgScal* __restrict__ sc, double* __restrict__ rzpart) {
+  extern __shared__ double sw64[];   // k x 32 chunk of w
+  __shared__ double sh[32];
+  const int c0 = blockIdx.y * 32;
+  const int nc = min(32, t - c0);
+  for (int idx = threadIdx.x; idx < k * 32; idx += blockDim.x) {
+    const int j = idx / 32, cc = idx % 32;
+    sw64[idx] = cc < nc ? w[j * t + c0 + cc] : 0.0;
+  }
+  __syncthreads();
+  bool act[32];
+#pragma unroll
+  for (int cc = 0; cc < 32; ++cc) act[cc] = cc < nc && (!sc || sc[c0 + cc].active);
+  const int nblk = gridDim.x;
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  double rz[32];
+#pragma unroll
+  for (int cc = 0; cc < 32; ++cc) rz[cc] = 0.0;
+  for (int64_t a = r0 + threadIdx.x; a < r1; a += blockDim.x) {
+    const double d = dh[a];
+    double acc[32];
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) acc[cc] = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double l = L[(int64_t)j * ldl + a] * d;
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) acc[cc] = fma(l, sw64[j * 32 + cc], acc[cc]);
+    }
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) {
+      if (!act[cc]) continue;
+      const int64_t o = (int64_t)(c0 + cc) * ld + a;
+      const float r = R[o];
+      const double z = d * fma(d, (double)r, -acc[cc]);
+      Z[o] = (float)z;
+      rz[cc] += (double)r * z;
+    }
+  }
+  if (rzpart) {
+    for (int cc = 0; cc < nc; ++cc) {
+      const double v = block_sum(rz[cc], sh);
+      if (threadIdx.x == 0) rzpart[(int64_t)(c0 + cc) * nblk + blockIdx.x] = v;
+    }
+  }
+}
+
 // ---- CG scalar kernels -------------------------------------------------------
 __global__ void cg_init_kernel(CgScal* sc, const double* __restrict__ bb,
                                const double* __restrict__ rzpart, int nblk, int t,
@@ -432,6 +539,29 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
                               const float* R, float* Z, int64_t ld, int t,
                               const CgScal* sc, double* rzpart) {
   const int k = pc ? pc->k : 0;
+  if (k > 0 && pc->dh64 && pc->L) {
+    // FP64 path (see ltr64_kernel)
+    const int nb = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 2048)));
+    double* part = ws<double>(ctx, WS_CG_G, (size_t)nb * k * t + (size_t)k * t);
+    double* w64 = ws<double>(ctx, WS_CG_W64, (size_t)k * t);
+    if (!part || !w64) return set_err(ctx, GP_ENOMEM, "workspace (precond)");
+    double* G = part + (size_t)nb * k * t;
+    ltr64_kernel<<<dim3(nb, k, (unsigned)ceil_div(t, 32)), 256, 0, ctx->stream>>>(pc->L, pc->n, k, R, ld, t, n, sc,
+                                                                                 pc->dh64, part);
+    GP_LAUNCHED(ctx);
+    const unsigned g2 = (unsigned)ceil_div((int64_t)k * t, 128);
+    g_reduce_kernel<<<g2, 128, 0, ctx->stream>>>(part, nb, k, t, sc, G);
+    GP_LAUNCHED(ctx);
+    w64_apply_kernel<<<g2, 128, 0, ctx->stream>>>(pc->cinv, G, k, t, w64);
+    GP_LAUNCHED(ctx);
+    const size_t shm = sizeof(double) * (size_t)k * 32;
+    if (shm > 48 * 1024)
+      GP_CUDA(ctx, cudaFuncSetAttribute(z64_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    z64_apply_kernel<<<dim3(kRedBlocks, (unsigned)ceil_div(t, 32)), 256, shm, ctx->stream>>>(
+        pc->L, pc->n, k, w64, t, R, Z, ld, n, pc->dh64, sc, rzpart);
+    GP_LAUNCHED(ctx);
+    return GP_OK;
+  }
   float* wf = nullptr;
   if (k > 0) {
     const int nb = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 256)));

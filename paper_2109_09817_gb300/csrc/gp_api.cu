@@ -300,6 +300,21 @@ int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
   return GP_OK;
 }
 
+int gp_bcg(gp_ctx* ctx, const float* X, int64_t N, int d, const gp_theta* theta, const double* L, int k,
+           const double* resid_diag, const float* B, int t, double tol, int max_iter, int precision,
+           float* Omega, int* iters, double* rel_resid) {
+  GP_TRY(check_common(ctx, X, N, d, theta));
+  if (!B || !Omega || t < 1 || t > 32 || max_iter < 1 || !(tol > 0.0) || k < 0 || (k > 0 && !L) ||
+      !valid_precision(precision))
+    return set_err(ctx, GP_EINVAL, "gp_bcg: bad arguments");
+  Prep p;
+  GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
+  Precond pc;
+  GP_TRY(precond_setup(ctx, L, N, k, k, theta->sigma2, resid_diag, &pc));
+  return bcg_run(ctx, p, theta->outputscale, theta->sigma2, pc, B, N, t, tol, max_iter, precision, Omega, N,
+                 iters, rel_resid);
+}
+
 int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
                    const gp_theta* theta, const double* L, int k,
                    const double* resid_diag, const float* B, int t, double tol,

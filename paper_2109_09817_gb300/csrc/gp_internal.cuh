@@ -45,6 +45,8 @@ enum WsSlot {
   WS_GR_U, WS_GR_W, WS_GR_ACC,
   WS_PR_K, WS_PR_O, WS_STATUS, WS_PC_DG, WS_PC_DH, WS_PC_RES,
   WS_RF_R, WS_RF_D, WS_RF_W, WS_RF_S, WS_GT_P, WS_GT_T,
+  WS_BC_C, WS_BC_P, WS_BC_W, WS_BC_S, WS_BC_R, WS_BC_RH, WS_BC_D, WS_BC_D2, WS_BC_DT,
+  WS_BC_WK, WS_BC_Q, WS_BC_OM, WS_BC_M, WS_BC_DH, WS_PC_DH64, WS_CG_W64,
   WS_COUNT
 };
 
@@ -184,6 +186,7 @@ struct Precond {
   const double* resid = nullptr; // residual diagonal (device, nullable)
   const float* L32 = nullptr;    // L~ = D^{-1/2} L in FP32, ld n_pad
   const float* dh = nullptr;     // D^{-1/2}, n_pad floats (0 on padding)
+  const double* dh64 = nullptr;  // D^{-1/2} in FP64, n_pad (0 on padding)
   int64_t ld32 = 0;
   const double* cfac = nullptr;  // k x k lower Cholesky of I + L~^T L~
   const double* cinv = nullptr;  // (I + L~^T L~)^{-1}, k x k, FP64
@@ -223,6 +226,11 @@ struct CgArgs {
   double* relres_dev = nullptr;  // device t
 };
 int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res);
+// Block CG on S^T K-hat S (AltBBMM, bcg.cu): B, Omega t <= 32 vectors (ld
+// ldb / ldo); iters_out, relres_out host.
+int bcg_run(gp_ctx* ctx, const Prep& p, double s_out, double sigma2, const Precond& pc, const float* B,
+            int64_t ldb, int t, double tol, int max_iter, int precision, float* Omega, int64_t ldo,
+            int* iters_out, double* relres_out);
 // Z = P^{-1} R for t vectors (ld ld), optional rz[c] += R_c . Z_c partials
 int precond_apply(gp_ctx* ctx, const Precond* pc, int64_t n, const float* R,
                   float* Z, int64_t ld, int t, const int* active,

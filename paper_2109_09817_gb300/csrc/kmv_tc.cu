@@ -513,7 +513,7 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   // launch order, so every row tile finishes band y before band y + 1 starts
   // and each band of X~_J / V_J is read from DRAM about once, instead of once
   // per wave of CTAs that have drifted apart.
-  const int64_t tile_bytes = (int64_t)BN * (DP + T) * 4 * (SPLIT ? 2 : 1) + 256;
+  const int64_t tile_bytes = (int64_t)BN * (DP + T) * 4 * (SPLIT ? 2 : 1) + (SPLIT ? (int64_t)BN * T * 2 : 0) + 256;
   const int64_t band_tiles = std::max<int64_t>(64, (48LL << 20) / tile_bytes);
   splits = std::max<int64_t>(splits, ceil_div(col_tiles, band_tiles));
   const int64_t per = ceil_div(col_tiles, splits);

@@ -277,15 +277,18 @@ __global__ void pc_small_inverse(const double* __restrict__ F, int k,
 
 // D_a = (resid_a or 0) + sigma2 (FP64), dh_a = D_a^{-1/2} (FP32, 0 on padding)
 __global__ void pc_diag_kernel(const double* __restrict__ resid, double sigma2, int64_t n,
-                               int64_t ld32, double* __restrict__ Dg, float* __restrict__ dh) {
+                               int64_t ld32, double* __restrict__ Dg, float* __restrict__ dh,
+                               double* __restrict__ dh64) {
   for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < ld32;
        a += (int64_t)gridDim.x * blockDim.x) {
     if (a < n) {
       const double D = (resid ? resid[a] : 0.0) + sigma2;
       Dg[a] = D;
-      dh[a] = (float)(1.0 / sqrt(D));
+      dh64[a] = 1.0 / sqrt(D);
+      dh[a] = (float)dh64[a];
     } else {
       dh[a] = 0.f;
+      dh64[a] = 0.0;
     }
   }
 }
@@ -375,14 +378,16 @@ int precond_setup(gp_ctx* ctx, const double* L, int64_t n, int k_alloc,
   (void)k_alloc;
   double* Dg = ws<double>(ctx, WS_PC_DG, (size_t)pc.ld32 + 512);
   float* dh = ws<float>(ctx, WS_PC_DH, (size_t)pc.ld32);
-  if (!Dg || !dh) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner diagonal)");
+  double* dh64 = ws<double>(ctx, WS_PC_DH64, (size_t)pc.ld32);
+  if (!Dg || !dh || !dh64) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner diagonal)");
   double* lpart = Dg + pc.ld32;   // 256 partial sums of log D
   const unsigned eg0 = (unsigned)std::min<int64_t>(ceil_div(pc.ld32, 256), 16LL * ctx->num_sms);
-  pc_diag_kernel<<<eg0, 256, 0, ctx->stream>>>(resid, sigma2, n, pc.ld32, Dg, dh);
+  pc_diag_kernel<<<eg0, 256, 0, ctx->stream>>>(resid, sigma2, n, pc.ld32, Dg, dh, dh64);
   GP_LAUNCHED(ctx);
   pc_logd_partial<<<256, 256, 0, ctx->stream>>>(Dg, n, lpart);
   GP_LAUNCHED(ctx);
   pc.dh = dh;
+  pc.dh64 = dh64;
   double* cf = ws<double>(ctx, WS_PC_CF, (size_t)2 * std::max(rank, 1) * std::max(rank, 1) + 8);
   if (!cf) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner)");
   double* cinv = cf + (size_t)rank * rank;

@@ -1,0 +1,98 @@
+"""AltBBMM block CG (gp_bcg) against the FP64 oracle's block CG and the
+Cholesky solution, through the C ABI.  Gates: true relative residual 1e-4
+(the solve tolerance), solution vs Cholesky 1e-3, block steps within 25 % + 3
+of the oracle's FP64 block CG on the same preconditioner."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import gp_oracle as go  # noqa: E402
+from synth import make_workload  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_09817_gb300 as gp_
+    return gp_
+
+
+@pytest.fixture(scope="module")
+def ctx(gp):
+    c = gp.Context(0)
+    yield c
+    c.close()
+
+
+def _theta(gp, w):
+    return gp.Theta(w.lengthscale, w.outputscale, w.sigma2)
+
+
+@pytest.mark.parametrize("resid", [False, True])
+def test_bcg_gp2k_matches_oracle(gp, ctx, resid):
+    w = make_workload("gp2k")
+    X = torch.from_numpy(w.X).cuda()
+    th = _theta(gp, w)
+    k = 32
+    out = gp.gp_pivchol(ctx, X, th, k, want_resid=resid)
+    L = out[0]
+    res_d = out[3] if resid else None
+    rng = np.random.default_rng(6)
+    B = np.vstack([w.y, rng.choice([-1.0, 1.0], size=(15, w.N))]).astype(np.float32)
+    r = gp.gp_bcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=1e-5, max_iter=500, resid=res_d)
+    assert r["rc"] == 0 and np.all(r["relres"] < 1e-5)
+    Om = r["Omega"].cpu().numpy().T.astype(np.float64)
+    true = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
+    assert true.max() <= 1e-4
+    Kh = go.khat_matrix(w.X, w.lengthscale, 1.0, w.sigma2)
+    ref = go.cholesky_solve(Kh, B.T.astype(np.float64))
+    err = np.linalg.norm(Om - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= 1e-3
+    Lr, pr, _ = go.pivoted_cholesky(w.X, w.lengthscale, 1.0, k)
+    rr = go.residual_diagonal(w.X, w.lengthscale, 1.0, Lr, pr) if resid else None
+    o = go.bcg(lambda V: Kh @ V, B.T.astype(np.float64), go.sym_precond_factor(Lr, w.sigma2, rr),
+               1e-5, 500)
+    assert abs(r["iters"] - o["iters"]) <= 0.25 * o["iters"] + 3, (r["iters"], o["iters"])
+
+
+def test_bcg_block_of_one_is_pcg(gp, ctx):
+    """Block size 1: CG on S^T K-hat S takes as many steps as PCG with P."""
+    w = make_workload("gp2k", N=1500, d=16)
+    X = torch.from_numpy(w.X).cuda()
+    th = _theta(gp, w)
+    L, _, _ = gp.gp_pivchol(ctx, X, th, 32)
+    b = torch.from_numpy(w.y[None, :].copy()).cuda()
+    a = gp.gp_bcg(ctx, X, th, L, b, tol=1e-5, max_iter=1000)
+    p = gp.gp_mbcg(ctx, X, th, L, b, tol=1e-5, max_iter=1000, precision=gp.GP_FP32_SPLIT_TF32)
+    assert a["rc"] == 0 and p["rc"] == 0
+    assert abs(a["iters"] - int(p["iters"][0])) <= 2 + 0.05 * p["iters"][0]
+
+
+def test_bcg_clustered_resid_form(gp, ctx):
+    w = make_workload("gp256k", N=4096)
+    X = torch.from_numpy(w.X).cuda()
+    th = _theta(gp, w)
+    L, _, _, res_d = gp.gp_pivchol(ctx, X, th, 64, want_resid=True)
+    rng = np.random.default_rng(7)
+    B = np.vstack([w.y, rng.choice([-1.0, 1.0], size=(7, w.N))]).astype(np.float32)
+    r = gp.gp_bcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=1e-4, max_iter=500, resid=res_d)
+    assert r["rc"] == 0
+    Om = r["Omega"].cpu().numpy().T.astype(np.float64)
+    true = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
+    assert true.max() <= 2e-4
+
+
+def test_bcg_rejects_bad_input(gp, ctx):
+    w = make_workload("gp2k", N=200, d=4)
+    X = torch.from_numpy(w.X).cuda()
+    th = _theta(gp, w)
+    B = torch.zeros((2, w.N), device="cuda")
+    B[0] = torch.from_numpy(w.y).cuda()
+    with pytest.raises(gp.GPError):
+        gp.gp_bcg(ctx, X, th, None, B)                      # zero column
+    with pytest.raises(gp.GPError):
+        gp.gp_bcg(ctx, X, th, None, torch.ones((33, w.N), device="cuda"))   # t > 32
