@@ -187,8 +187,11 @@ GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
  * ||B_c - K-hat Omega_c|| / ||B_c|| (by its recurrence) is below tol.
  * B, Omega: device, N x t column-major (ld N), 1 <= t <= 32, no zero column
  * (GP_EINVAL).  iters (host int, nullable): block steps taken; rel_resid
- * (host t doubles, nullable).  GP_ENOTCONV after max_iter steps (Omega holds
- * the last iterate); GP_EBREAKDOWN if a block Gram matrix loses definiteness.
+ * (host t doubles, nullable).  The s x s systems are solved by pseudo-inverse
+ * (directions below 1e-10 of the largest eigenvalue are dropped), so columns
+ * that converge or become dependent get zero steps.  GP_ENOTCONV after
+ * max_iter steps (Omega holds the last iterate); GP_EBREAKDOWN if a block
+ * Gram matrix vanishes.
  * Synchronises every step. */
 GP_API int gp_bcg(gp_ctx* ctx, const float* X, int64_t N, int d,
                   const gp_theta* theta, const double* L, int k,
@@ -271,12 +274,18 @@ GP_API int gp_kmatmul_noalloc(const float* X, int64_t N, int d,
                               float* out, void* stream);
 
 /* ---- trained model and prediction (Eq. pred) ------------------------------
- * gp_model_fit keeps, on the device, the prepared features, a = K-hat^{-1} y
- * (mBCG to `tol`), the preconditioner factor and the hyperparameters.
- * X and y are copied; the caller may free them afterwards.  Synchronises. */
+ * gp_model_fit keeps, on the device, the prepared features, a = K-hat^{-1} y,
+ * the preconditioner factor and the hyperparameters.  block = 1: a by
+ * preconditioned CG on y alone (mBCG to `tol`); 2 <= block <= 32: AltBBMM
+ * (Sec. 3.1-3.2), block CG on [y | block - 1 random right-hand sides] with
+ * the symmetric Nystrom preconditioner (as gp_bcg), stopping when y's
+ * residual is below tol; a = column 0 (the block Krylov space contains y's
+ * own, so y converges in fewer steps; a product costs the same for up to 16
+ * vectors).  X and y are copied; the caller may free them afterwards.
+ * GP_ENOTCONV / GP_EBREAKDOWN: no model is returned.  Synchronises. */
 GP_API int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
-                 const gp_theta* theta, const float* y, int k, int precond, double tol,
-                 int max_iter, int precision, gp_model** out,
+                 const gp_theta* theta, const float* y, int k, int precond, int block,
+                 double tol, int max_iter, int precision, gp_model** out,
                  gp_stats* stats);
 GP_API void gp_model_free(gp_model* model);
 
@@ -312,7 +321,8 @@ typedef struct gp_server gp_server;
  * streams cannot be set up. */
 GP_API int gp_server_create(gp_server** out, int device, int64_t max_batch_rows,
                             double reserve_bytes);
-/* Fit a model from DEVICE arrays X (N x d) and y (N) as gp_model_fit does,
+/* Fit a model from DEVICE arrays X (N x d) and y (N) as gp_model_fit does
+ * (block = 1),
  * keep it resident and start its batching thread; *model_id is its index.
  * Synchronises; errors as gp_model_fit (message in gp_server_last_error). */
 GP_API int gp_server_add_model(gp_server* srv, const float* X, int64_t N, int d,

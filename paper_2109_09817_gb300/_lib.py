@@ -80,8 +80,8 @@ def load(path: str = LIB_PATH):
                                    c_dbl, c_int, c_int, c_int, c_int, vp, ip, ip, dp]),
         "gp_logml_and_grad": (c_int, [vp, vp, i64, c_int, th, vp, c_int, ctypes.c_uint64,
                                       c_int, c_int, c_dbl, c_int, c_int, dp, dp, dp, dp, st]),
-        "gp_model_fit": (c_int, [vp, vp, i64, c_int, th, vp, c_int, c_int, c_dbl, c_int, c_int,
-                                 ctypes.POINTER(vp), st]),
+        "gp_model_fit": (c_int, [vp, vp, i64, c_int, th, vp, c_int, c_int, c_int, c_dbl, c_int,
+                                 c_int, ctypes.POINTER(vp), st]),
         "gp_model_free": (None, [vp]),
         "gp_predict": (c_int, [vp, vp, vp, i64, vp, vp, c_int]),
         "gp_kmatmul_noalloc": (c_int, [vp, i64, c_int, th, vp, c_int, vp, vp]),

@@ -270,7 +270,7 @@ class Model:
 
     def __init__(self, ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tensor,
                  k: int = 32, tol: float = 1e-6, max_iter: int = 1000,
-                 precision: int = GP_FP32_PLAIN, precond: int = GP_PC_SIGMA):
+                 precision: int = GP_FP32_PLAIN, precond: int = GP_PC_SIGMA, block: int = 1):
         _dev(ctx, X, torch.float32, "X")
         _dev(ctx, y, torch.float32, "y")
         self.ctx = ctx
@@ -279,7 +279,7 @@ class Model:
         h = ctypes.c_void_p()
         stats = _lib.GpStats()
         th, keep = theta.as_c()
-        ctx.check(ctx.lib.gp_model_fit(ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), k, precond, tol,
+        ctx.check(ctx.lib.gp_model_fit(ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), k, precond, block, tol,
                                        max_iter, precision, ctypes.byref(h), ctypes.byref(stats)))
         self.h = h
         self.stats = stats.as_dict()
@@ -297,8 +297,8 @@ class Model:
 
 
 def gp_model_fit(ctx: Context, X, theta, y, k=32, tol=1e-6, max_iter=1000,
-                 precision=GP_FP32_PLAIN, precond=GP_PC_SIGMA) -> Model:
-    return Model(ctx, X, theta, y, k, tol, max_iter, precision, precond)
+                 precision=GP_FP32_PLAIN, precond=GP_PC_SIGMA, block=1) -> Model:
+    return Model(ctx, X, theta, y, k, tol, max_iter, precision, precond, block)
 
 
 def gp_predict(ctx: Context, model: Model, Xp: torch.Tensor, var_mode: int = GP_VAR_NONE):

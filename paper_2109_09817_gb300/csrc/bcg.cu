@@ -220,34 +220,32 @@ void jacobi_eigh(std::vector<double>& A, int k, std::vector<double>& lam, std::v
   for (int i = 0; i < k; ++i) lam[i] = A[(size_t)i * k + i];
 }
 
-// X = A^{-1} B for SPD A (t x t) by Cholesky; false if A is not PD.
-bool spd_solve(std::vector<double> A, const std::vector<double>& B, int t, std::vector<double>& X) {
-  for (int c = 0; c < t; ++c) {
-    double dg = A[(size_t)c * t + c];
-    for (int j = 0; j < c; ++j) dg -= A[(size_t)c * t + j] * A[(size_t)c * t + j];
-    if (!(dg > 0.0)) return false;
-    dg = std::sqrt(dg);
-    A[(size_t)c * t + c] = dg;
-    for (int r = c + 1; r < t; ++r) {
-      double v = A[(size_t)r * t + c];
-      for (int j = 0; j < c; ++j) v -= A[(size_t)r * t + j] * A[(size_t)c * t + j];
-      A[(size_t)r * t + c] = v / dg;
+// X = A^+ B for a symmetric positive semidefinite t x t A: eigenpairs by
+// cyclic Jacobi, eigenvalues below rel * max dropped.  When columns of the
+// block converge or become dependent (FP32 vectors), the block Gram
+// matrices turn singular; dropping those directions gives them zero steps
+// instead of a breakdown.  Returns the number of directions kept.
+int psd_solve(const std::vector<double>& A, const std::vector<double>& B, int t, double rel,
+              std::vector<double>& X) {
+  std::vector<double> a((size_t)t * t), lam, V;
+  for (int i = 0; i < t; ++i)       // symmetrise (FP32 products: A is symmetric to ~1e-7)
+    for (int j = 0; j < t; ++j) a[(size_t)i * t + j] = 0.5 * (A[(size_t)i * t + j] + A[(size_t)j * t + i]);
+  jacobi_eigh(a, t, lam, V);
+  double mx = 0.0;
+  for (double l : lam) mx = std::max(mx, l);
+  X.assign((size_t)t * t, 0.0);
+  int kept = 0;
+  for (int q = 0; q < t; ++q) {
+    if (!(lam[q] > rel * mx)) continue;
+    ++kept;
+    for (int c = 0; c < t; ++c) {
+      double proj = 0.0;   // v_q^T B[:, c]
+      for (int i = 0; i < t; ++i) proj += V[(size_t)i * t + q] * B[(size_t)i * t + c];
+      proj /= lam[q];
+      for (int i = 0; i < t; ++i) X[(size_t)i * t + c] += V[(size_t)i * t + q] * proj;
     }
   }
-  X = B;
-  for (int col = 0; col < t; ++col) {
-    for (int r = 0; r < t; ++r) {   // forward
-      double v = X[(size_t)r * t + col];
-      for (int j = 0; j < r; ++j) v -= A[(size_t)r * t + j] * X[(size_t)j * t + col];
-      X[(size_t)r * t + col] = v / A[(size_t)r * t + r];
-    }
-    for (int r = t - 1; r >= 0; --r) {   // backward
-      double v = X[(size_t)r * t + col];
-      for (int j = r + 1; j < t; ++j) v -= A[(size_t)j * t + r] * X[(size_t)j * t + col];
-      X[(size_t)r * t + col] = v / A[(size_t)r * t + r];
-    }
-  }
-  return true;
+  return kept;
 }
 
 struct SymApply {
@@ -303,7 +301,7 @@ int update(gp_ctx* ctx, const float* base, const float* X, const float* M, int64
 
 int bcg_run(gp_ctx* ctx, const Prep& p, double s_out, double sigma2, const Precond& pc, const float* B,
             int64_t ldb, int t, double tol, int max_iter, int precision, float* Omega, int64_t ldo,
-            int* iters_out, double* relres_out) {
+            int* iters_out, double* relres_out, int stop_col) {
   if (t < 1 || t > 32) return set_err(ctx, GP_EINVAL, "gp_bcg: 1 <= t <= 32");
   const int64_t n = p.n, ld = p.n_pad;
   cudaStream_t st = ctx->stream;
@@ -402,7 +400,8 @@ int bcg_run(gp_ctx* ctx, const Prep& p, double s_out, double sigma2, const Preco
     GP_CUDA(ctx, cudaStreamSynchronize(st));
     GP_TRY(check_status(ctx));
     std::vector<double> gam(h, h + tt), alpha;
-    if (!spd_solve(gam, rho, t, alpha)) return set_err(ctx, GP_EBREAKDOWN, "gp_bcg: D^T A D not positive definite");
+    if (psd_solve(gam, rho, t, 1e-10, alpha) == 0)
+      return set_err(ctx, GP_EBREAKDOWN, "gp_bcg: D^T A D vanished");
     // alpha is t x t with row index = direction column, col index = rhs column
     GP_TRY(put_matrix(0, alpha, 1.0));
     GP_TRY(update(ctx, Om, Dt, Mf, ld, n, t, Om));
@@ -418,7 +417,7 @@ int bcg_run(gp_ctx* ctx, const Prep& p, double s_out, double sigma2, const Preco
     bool all = true;
     for (int c = 0; c < t; ++c) {
       relres[c] = std::sqrt(std::max(h[1024 + c], 0.0)) / bnorm[c];
-      all = all && relres[c] < tol;
+      if (stop_col < 0 || c == stop_col) all = all && relres[c] < tol;
     }
     std::vector<double> rho_new(h, h + tt);
     if (all) {
@@ -426,7 +425,8 @@ int bcg_run(gp_ctx* ctx, const Prep& p, double s_out, double sigma2, const Preco
       break;
     }
     std::vector<double> beta;
-    if (!spd_solve(rho, rho_new, t, beta)) return set_err(ctx, GP_EBREAKDOWN, "gp_bcg: Rh^T Rh not positive definite");
+    if (psd_solve(rho, rho_new, t, 1e-10, beta) == 0)
+      return set_err(ctx, GP_EBREAKDOWN, "gp_bcg: Rh^T Rh vanished");
     GP_TRY(put_matrix(2, beta, 1.0));
     GP_TRY(update(ctx, Rh, D, Mf + 2048, ld, n, t, D2));
     std::swap(D, D2);

@@ -312,7 +312,7 @@ int gp_bcg(gp_ctx* ctx, const float* X, int64_t N, int d, const gp_theta* theta,
   Precond pc;
   GP_TRY(precond_setup(ctx, L, N, k, k, theta->sigma2, resid_diag, &pc));
   return bcg_run(ctx, p, theta->outputscale, theta->sigma2, pc, B, N, t, tol, max_iter, precision, Omega, N,
-                 iters, rel_resid);
+                 iters, rel_resid, -1);
 }
 
 int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
@@ -573,11 +573,11 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
 }
 
 int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
-                 const gp_theta* theta, const float* y, int k, int precond, double tol,
+                 const gp_theta* theta, const float* y, int k, int precond, int block, double tol,
                  int max_iter, int precision, gp_model** out, gp_stats* stats) {
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!y || !out || k < 0 || k > N || max_iter < 1 || !valid_precision(precision) ||
-      (precond != GP_PC_SIGMA && precond != GP_PC_RESID))
+      (precond != GP_PC_SIGMA && precond != GP_PC_RESID) || block < 1 || block > 32)
     return set_err(ctx, GP_EINVAL, "gp_model_fit: bad arguments");
   *out = nullptr;
   Prep p;
@@ -666,6 +666,38 @@ int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
   }
   // a = K-hat^{-1} y
   GP_CUDA(ctx, cudaMemsetAsync(m->alpha, 0, sizeof(float) * p.n_pad, st));
+  if (block > 1) {
+    // AltBBMM (Sec. 3.1-3.2): y and block - 1 random right-hand sides share
+    // one block Krylov space, which contains y's own; a = column 0
+    const int64_t ldb = p.n_pad;
+    float* Bb = ws<float>(ctx, WS_RF_R, (size_t)block * ldb);
+    float* Ob = ws<float>(ctx, WS_RF_D, (size_t)block * ldb);
+    if (!Bb || !Ob) return fail(set_err(ctx, GP_ENOMEM, "workspace (block fit)"));
+    if (cudaMemsetAsync(Bb, 0, sizeof(float) * (size_t)block * ldb, st) != cudaSuccess)
+      return fail(check_cuda(ctx, cudaGetLastError(), "cudaMemsetAsync"));
+    int rc = copy_vectors(ctx, y, N, Bb, ldb, N, 1, 1.f);
+    if (rc == GP_OK) rc = probe_vectors(ctx, m->L, N, rank, m->sigma2, resid, 0x5eedULL, block - 1, Bb + ldb, ldb);
+    if (rc != GP_OK) return fail(rc);
+    int iters = 0;
+    std::vector<double> rel(block, 0.0);
+    rc = bcg_run(ctx, mp, m->s, m->sigma2, pc, Bb, ldb, block, tol, max_iter, precision, Ob, ldb, &iters,
+                 rel.data(), 0);
+    if (rc != GP_OK) return fail(rc);
+    rc = copy_vectors(ctx, Ob, ldb, m->alpha, p.n_pad, N, 1, 1.f);
+    if (rc != GP_OK) return fail(rc);
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      stats->iters_max = stats->iters_y = iters;
+      stats->rank = rank;
+      stats->n_kmatmul = iters;
+      stats->relres_y = rel[0];
+      stats->relres_max = *std::max_element(rel.begin(), rel.end());
+      stats->logdet_P = pc.logdet;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(check_cuda(ctx, cudaGetLastError(), "sync"));
+    *out = m;
+    return GP_OK;
+  }
   double* ah = ws<double>(ctx, WS_CG_AH, (size_t)max_iter);
   double* bh = ws<double>(ctx, WS_CG_BH, (size_t)max_iter);
   int* rec = static_cast<int*>(ws_get(ctx, WS_GR_ACC, 256));

@@ -227,10 +227,11 @@ struct CgArgs {
 };
 int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res);
 // Block CG on S^T K-hat S (AltBBMM, bcg.cu): B, Omega t <= 32 vectors (ld
-// ldb / ldo); iters_out, relres_out host.
+// ldb / ldo); iters_out, relres_out host; stop_col < 0: stop when every
+// column is below tol, else when column stop_col is.
 int bcg_run(gp_ctx* ctx, const Prep& p, double s_out, double sigma2, const Precond& pc, const float* B,
             int64_t ldb, int t, double tol, int max_iter, int precision, float* Omega, int64_t ldo,
-            int* iters_out, double* relres_out);
+            int* iters_out, double* relres_out, int stop_col);
 // Z = P^{-1} R for t vectors (ld ld), optional rz[c] += R_c . Z_c partials
 int precond_apply(gp_ctx* ctx, const Precond* pc, int64_t n, const float* R,
                   float* Z, int64_t ld, int t, const int* active,

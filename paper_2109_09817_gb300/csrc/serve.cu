@@ -226,7 +226,7 @@ void solve_loop(gp_server* srv) {
       rc = GP_ECUDA;
     if (rc == GP_OK) {
       gp_theta th{r->ell.data(), r->s, r->sigma2};
-      rc = gp_model_fit(srv->solve_ctx, dx, r->n, r->d, &th, dy, r->k, GP_PC_RESID, r->tol, r->max_iter,
+      rc = gp_model_fit(srv->solve_ctx, dx, r->n, r->d, &th, dy, r->k, GP_PC_RESID, 1, r->tol, r->max_iter,
                         GP_FP32_SPLIT_TF32, &m, nullptr);
     }
     if (rc == GP_OK) {
@@ -293,7 +293,8 @@ int gp_server_add_model(gp_server* srv, const float* X, int64_t N, int d, const 
     cudaStreamDestroy(st);
     return srv_err(srv, GP_ECUDA, "context creation failed");
   }
-  int rc = gp_model_fit(sl->ctx, X, N, d, theta, y, k, precond, tol, max_iter, precision, &sl->model, nullptr);
+  int rc = gp_model_fit(sl->ctx, X, N, d, theta, y, k, precond, 1, tol, max_iter, precision, &sl->model,
+                        nullptr);
   if (rc != GP_OK) {
     std::string msg = gp_last_error(sl->ctx);
     gp_destroy(sl->ctx);

@@ -96,3 +96,23 @@ def test_bcg_rejects_bad_input(gp, ctx):
         gp.gp_bcg(ctx, X, th, None, B)                      # zero column
     with pytest.raises(gp.GPError):
         gp.gp_bcg(ctx, X, th, None, torch.ones((33, w.N), device="cuda"))   # t > 32
+
+
+def test_model_fit_block_converges_faster_and_predicts(gp, ctx):
+    """gp_model_fit with block = 16 (AltBBMM): y converges within the block
+    in no more steps than PCG on y alone, and the predictive mean matches
+    the oracle (1e-4)."""
+    w = make_workload("gp2k")
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(w.y).cuda()
+    th = _theta(gp, w)
+    m1 = gp.gp_model_fit(ctx, X, th, y, k=32, tol=1e-6, max_iter=2000,
+                         precision=gp.GP_FP32_SPLIT_TF32, precond=gp.GP_PC_RESID, block=1)
+    m16 = gp.gp_model_fit(ctx, X, th, y, k=32, tol=1e-6, max_iter=2000,
+                          precision=gp.GP_FP32_SPLIT_TF32, precond=gp.GP_PC_RESID, block=16)
+    assert m16.stats["iters_y"] <= m1.stats["iters_y"], (m16.stats, m1.stats)
+    mean, _ = gp.gp_predict(ctx, m16, torch.from_numpy(w.Xtest).cuda())
+    mr, _ = go.predict(w.X, w.y.astype(np.float64), w.Xtest, w.lengthscale, 1.0, w.sigma2)
+    assert np.linalg.norm(mean.cpu().numpy() - mr) <= 1e-4 * np.linalg.norm(mr)
+    m1.free()
+    m16.free()
