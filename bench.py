@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gp1m", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="split_tf32",
-                    choices=["fp32", "split_tf32", "split_bf16", "tf32", "bf16"])
+                    choices=["fp32", "split_tf32", "split_f16", "tf32"])
     ap.add_argument("--precond", default="auto", choices=["auto", "sigma", "resid"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -136,10 +136,11 @@ def load_peaks():
 
 def tensor_flops_per_entry(precision: str, d: int, t: int) -> float:
     """Tensor-pipe work per kernel entry of one K-hat V product: the cross
-    term (2d) and the contraction (2t), each as three TF32 products in the
-    split form (hi.hi + hi.lo + lo.hi) and one in the single TF32 form."""
+    term (2d) and the contraction (2t), each as three products in the split
+    forms (hi.hi + hi.lo + lo.hi; TF32 or FP16 parts) and one in the single
+    TF32 form."""
     per = 2.0 * (d + t)
-    return 3.0 * per if precision == "split_tf32" else per
+    return 3.0 * per if precision in ("split_tf32", "split_f16") else per
 
 
 def roofline(precision: str, d: int, t: int, entries_per_s: float, sm_mhz: float, peaks: dict,
@@ -147,7 +148,9 @@ def roofline(precision: str, d: int, t: int, entries_per_s: float, sm_mhz: float
     """Roofline of the fused K-hat V kernel.
 
     Tensor-core forms: achieved = N^2 x tensor FLOPs per entry / kernel time,
-    against the dense TF32 peak (measured BF16 burst x 1.1/2.25).  Plain FP32
+    against the dense peak of the operand type: FP16 runs at the BF16 rate
+    (the measured BF16 burst), TF32 at the measured BF16 burst x 1.1/2.25.
+    Plain FP32
     form: bound by the FMA/ALU pipes at d + t + 12 FP32 ops per entry on 128
     lanes per SM-clock (derived; no measured FP32 peak)."""
     if precision == "fp32":
@@ -159,10 +162,14 @@ def roofline(precision: str, d: int, t: int, entries_per_s: float, sm_mhz: float
                 "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)"}
     fl = tensor_flops_per_entry(precision, d, t)
     achieved = entries_per_s * fl / 1e12
-    peak = peaks["bf16_tflops"] * TF32_PER_BF16
+    if precision == "split_f16":
+        peak = peaks["bf16_tflops"]
+        basis = f"FP16 = BF16 burst {peaks['bf16_tflops']} ({peak_src}), same dense rate"
+    else:
+        peak = peaks["bf16_tflops"] * TF32_PER_BF16
+        basis = f"TF32 = BF16 burst {peaks['bf16_tflops']} ({peak_src}) x 1.1/2.25"
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "per_entry": f"{fl:.0f} tensor FLOPs",
-            "peak_basis": f"TF32 = BF16 burst {peaks['bf16_tflops']} ({peak_src}) x 1.1/2.25"}
+            "frac": achieved / peak, "per_entry": f"{fl:.0f} tensor FLOPs", "peak_basis": basis}
 
 
 def cpu_baseline(w, t, n_products, budget_s=12.0):
@@ -352,8 +359,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "split_tf32": "tf32x3/f32", "split_bf16": "bf16x3/f32",
-                  "tf32": "tf32/f32", "bf16": "bf16/f32"}[args.precision],
+        "dtype": {"fp32": "f32", "split_tf32": "tf32x3/f32", "split_f16": "f16x3/f32",
+                  "tf32": "tf32/f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: N={w.N}, d={w.d}, t=1+{npr}, k={k}, tol={tol}",
                    "precision": args.precision, "preconditioner": f"rank {k}, {pc_name} form",

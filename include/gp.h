@@ -64,10 +64,15 @@ enum {
   GP_FP32_SPLIT_TF32 = 1, /* tcgen05 kind::tf32, hi+lo split operands
                              (3 products) for both the cross term X X^T and
                              the contraction K V: FP32-class accuracy       */
-  GP_BF16_SPLIT = 2,      /* tcgen05 kind::f16 (bf16) hi+lo split, both
-                             contractions                                   */
-  GP_TF32 = 3,            /* tcgen05 kind::tf32, single-pass operands       */
-  GP_BF16 = 4             /* tcgen05 kind::f16 (bf16), single-pass          */
+  GP_FP32_SPLIT_F16 = 2,  /* tcgen05 kind::f16 with FP16 hi+lo split operands
+                             (3 products) for both contractions.  Operands
+                             are scaled by powers of two (features: one
+                             factor for the whole matrix; vectors: one per
+                             vector; K: 2^14) so that FP16's range holds
+                             them; the split then keeps 22 significant bits
+                             as the TF32 split does, at twice the reduction
+                             depth per MMA.  Needs d <= 64.                 */
+  GP_TF32 = 3             /* tcgen05 kind::tf32, single-pass operands       */
 };
 
 /* preconditioner forms (P = L L^T + D, L from the rank-k pivoted Cholesky) */
@@ -132,7 +137,8 @@ GP_API int gp_profile_read(gp_ctx* ctx, int64_t* products, double* ms,
  * out = (K(X, X) + sigma^2 I) V, with K formed tile by tile from X and
  * never stored.  X: N x d row-major.  V, out: t vectors of length N,
  * column-major.  1 <= t <= 512.  `precision` is one of GP_FP32_PLAIN ...
- * GP_BF16.  out must not alias V. */
+ * GP_TF32; the tensor-core forms need d <= 64 (GP_EINVAL otherwise).  out
+ * must not alias V. */
 GP_API int gp_kmatmul(gp_ctx* ctx, const float* X, int64_t N, int d,
                const gp_theta* theta, const float* V, int t, float* out,
                int precision);

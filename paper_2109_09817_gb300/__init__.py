@@ -8,7 +8,7 @@ hyperparameter gradients and prediction.  All arithmetic runs in libgp
 binding.  Importing it does not load the library; the first Context does,
 and fails loudly if libgp.so has not been built.
 """
-from ._lib import (GP_BF16, GP_BF16_SPLIT, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
+from ._lib import (GP_FP32_SPLIT_F16, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
                    GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_PC_SIGMA, GP_PC_RESID, EXPORTS,
                    LIB_PATH)
 

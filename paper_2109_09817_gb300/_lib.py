@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libgp.so")
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ENOTCONV, GP_EBREAKDOWN, GP_ENONPD, GP_ETIMEOUT, GP_ECUDA = range(8)
 ERROR_NAMES = {0: "GP_OK", 1: "GP_EINVAL", 2: "GP_ENOMEM", 3: "GP_ENOTCONV",
                4: "GP_EBREAKDOWN", 5: "GP_ENONPD", 6: "GP_ETIMEOUT", 7: "GP_ECUDA"}
-GP_FP32_PLAIN, GP_FP32_SPLIT_TF32, GP_BF16_SPLIT, GP_TF32, GP_BF16 = range(5)
+GP_FP32_PLAIN, GP_FP32_SPLIT_TF32, GP_FP32_SPLIT_F16, GP_TF32 = range(4)
 GP_VAR_NONE, GP_VAR_EXACT = 0, 1
 GP_PC_SIGMA, GP_PC_RESID = 0, 1
 

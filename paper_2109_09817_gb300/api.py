@@ -17,12 +17,12 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (GP_BF16, GP_BF16_SPLIT, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
+from ._lib import (GP_FP32_SPLIT_F16, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
                    GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_OK, GP_ENOTCONV,
                    GP_EBREAKDOWN, GP_EINVAL, GP_PC_SIGMA, GP_PC_RESID, ERROR_NAMES)
 
 PRECISIONS = {"fp32": GP_FP32_PLAIN, "split_tf32": GP_FP32_SPLIT_TF32,
-              "split_bf16": GP_BF16_SPLIT, "tf32": GP_TF32, "bf16": GP_BF16}
+              "split_f16": GP_FP32_SPLIT_F16, "tf32": GP_TF32}
 
 
 class GPError(RuntimeError):

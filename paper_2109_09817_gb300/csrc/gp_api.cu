@@ -123,7 +123,7 @@ int prep_train(gp_ctx* ctx, const float* X, int64_t N, int d,
   return prepare_features(ctx, X, N, d, mu, theta->lengthscale, precision, WS_XT, p);
 }
 
-bool valid_precision(int p) { return p >= GP_FP32_PLAIN && p <= GP_BF16; }
+bool valid_precision(int p) { return p >= GP_FP32_PLAIN && p <= GP_TF32; }
 
 }  // namespace
 }  // namespace gp
@@ -324,7 +324,8 @@ int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!B || !Omega || t < 1 || t > kMaxT || max_iter < 1 || max_outer < 1 || !(tol > 0.0) ||
       !(inner_tol > 0.0) || k < 0 || (k > 0 && !L) || !valid_precision(inner_precision) ||
-      (outer_precision != GP_FP32_PLAIN && outer_precision != GP_FP32_SPLIT_TF32))
+      (outer_precision != GP_FP32_PLAIN && outer_precision != GP_FP32_SPLIT_TF32 &&
+       outer_precision != GP_FP32_SPLIT_F16))
     return set_err(ctx, GP_EINVAL, "gp_mbcg_refine: bad arguments");
   cudaStream_t st = ctx->stream;
   // outer products on the accurate features, inner ones on a second family
@@ -617,19 +618,27 @@ int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
     GP_CUDA(ctx, cudaMemcpyAsync(m->xt_hi, p.xt_hi, sizeof(float) * ne, cudaMemcpyDeviceToDevice, st));
     GP_CUDA(ctx, cudaMemcpyAsync(m->xt_lo, p.xt_lo, sizeof(float) * ne, cudaMemcpyDeviceToDevice, st));
   }
-  if (p.xb_hi) {
-    if (cudaMalloc(&m->xb_hi, 2 * ne) != cudaSuccess || cudaMalloc(&m->xb_lo, 2 * ne) != cudaSuccess)
+  if (p.xh_hi) {
+    const size_t nh = (size_t)p.n_pad * kHalfCols;
+    if (cudaMalloc(&m->xh_hi, sizeof(__half) * nh) != cudaSuccess ||
+        cudaMalloc(&m->xh_lo, sizeof(__half) * nh) != cudaSuccess ||
+        cudaMalloc(&m->norm_h, sizeof(float) * p.n_pad) != cudaSuccess ||
+        cudaMalloc(&m->xh_scale, sizeof(float)) != cudaSuccess)
       return fail(set_err(ctx, GP_ENOMEM, "model allocation"));
-    GP_CUDA(ctx, cudaMemcpyAsync(m->xb_hi, p.xb_hi, 2 * ne, cudaMemcpyDeviceToDevice, st));
-    GP_CUDA(ctx, cudaMemcpyAsync(m->xb_lo, p.xb_lo, 2 * ne, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->xh_hi, p.xh_hi, sizeof(__half) * nh, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->xh_lo, p.xh_lo, sizeof(__half) * nh, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->norm_h, p.norm_h, sizeof(float) * p.n_pad, cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(m->xh_scale, p.xh_scale, sizeof(float), cudaMemcpyDeviceToDevice, st));
   }
   Prep mp = p;
   mp.xt = m->xt;
   mp.norm = m->norm;
   mp.xt_hi = m->xt_hi;
   mp.xt_lo = m->xt_lo;
-  mp.xb_hi = m->xb_hi;
-  mp.xb_lo = m->xb_lo;
+  mp.xh_hi = m->xh_hi;
+  mp.xh_lo = m->xh_lo;
+  mp.norm_h = m->norm_h;
+  mp.xh_scale = m->xh_scale;
   // preconditioner
   int rank = 0;
   double* resid = nullptr;
@@ -749,7 +758,8 @@ void gp_model_free(gp_model* m) {
   cudaSetDevice(m->device);
   cudaDeviceSynchronize();
   for (void* q : {(void*)m->mu, (void*)m->xt, (void*)m->norm, (void*)m->xt_hi,
-                  (void*)m->xt_lo, (void*)m->xb_hi, (void*)m->xb_lo, (void*)m->alpha,
+                  (void*)m->xt_lo, (void*)m->xh_hi, (void*)m->xh_lo, (void*)m->norm_h,
+                  (void*)m->xh_scale, (void*)m->alpha,
                   (void*)m->L, (void*)m->L32, (void*)m->cfac, (void*)m->dh})
     if (q) cudaFree(q);
   delete m;
@@ -769,8 +779,10 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, const float* Xp, int64_t M,
   mp.norm = m->norm;
   mp.xt_hi = m->xt_hi;
   mp.xt_lo = m->xt_lo;
-  mp.xb_hi = m->xb_hi;
-  mp.xb_lo = m->xb_lo;
+  mp.xh_hi = m->xh_hi;
+  mp.xh_lo = m->xh_lo;
+  mp.norm_h = m->norm_h;
+  mp.xh_scale = m->xh_scale;
   Prep q;
   GP_TRY(prepare_features(ctx, Xp, M, m->d, m->mu, m->ell.data(), m->precision, WS_XT2, &q));
   GP_TRY(kmv(ctx, q, mp, m->alpha, m->n_pad, 1, mean, M, m->s, 0.0, false, m->precision));

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -30,14 +31,18 @@ constexpr float kC2 = 0.16014921423310860f;      // (ln 2)^2 / 3
 
 constexpr int kRowPad = 256;   // rows of prepared arrays are padded to this
 constexpr int kColPad = 32;    // features are padded to this (zeros)
+constexpr int kHalfCols = 64;  // width of the FP16 split feature arrays (zeros)
+constexpr int kHalfTop = 15;   // FP16 operands are scaled into [2^14, 2^15)
+constexpr int kKExp = 14;      // K entries (<= 1) are held as 2^14 K in FP16
 constexpr int kMaxT = 512;
 
 // Workspace slots owned by a context.  Each grows on demand.
 enum WsSlot {
   WS_MU = 0, WS_SCALE, WS_PART,
-  WS_XT, WS_NORM, WS_XT_HI, WS_XT_LO, WS_XB_HI, WS_XB_LO,          // rows
-  WS_XT2, WS_NORM2, WS_XT2_HI, WS_XT2_LO, WS_XB2_HI, WS_XB2_LO,    // cross rows
-  WS_VHI, WS_VLO, WS_VBHI, WS_VBLO, WS_VPAD,
+  // two families of prepared features with the same layout (rows, cross rows)
+  WS_XT, WS_NORM, WS_XT_HI, WS_XT_LO, WS_XH_HI, WS_XH_LO, WS_NORMH, WS_XH_SC,
+  WS_XT2, WS_NORM2, WS_XT2_HI, WS_XT2_LO, WS_XH2_HI, WS_XH2_LO, WS_NORMH2, WS_XH2_SC,
+  WS_VHI, WS_VLO, WS_VBHI, WS_VBLO, WS_VPAD, WS_VMAX,
   WS_CG_U, WS_CG_R, WS_CG_Z, WS_CG_D, WS_CG_W, WS_CG_Z0, WS_CG_B,
   WS_CG_SCAL, WS_CG_PART, WS_CG_AH, WS_CG_BH, WS_CG_G,
   WS_PC_L, WS_PC_L32, WS_PC_D, WS_PC_PIV, WS_PC_STATE, WS_PC_GRAM, WS_PC_CF,
@@ -71,8 +76,10 @@ struct gp_model {
   float* norm = nullptr;
   float* xt_hi = nullptr;
   float* xt_lo = nullptr;
-  __nv_bfloat16* xb_hi = nullptr;
-  __nv_bfloat16* xb_lo = nullptr;
+  __half* xh_hi = nullptr;
+  __half* xh_lo = nullptr;
+  float* norm_h = nullptr;
+  float* xh_scale = nullptr;
   float* alpha = nullptr;      // n_pad, zero padded
   double* L = nullptr;         // n x k
   int k = 0;
@@ -142,8 +149,12 @@ struct Prep {
   const float* norm = nullptr;    // n_pad
   const float* xt_hi = nullptr;   // TF32-representable hi part (FP32 storage)
   const float* xt_lo = nullptr;   // TF32 lo part
-  const __nv_bfloat16* xb_hi = nullptr;
-  const __nv_bfloat16* xb_lo = nullptr;
+  // FP16 split (GP_FP32_SPLIT_F16): hi + lo = 2^e x~ to 22 bits, n_pad x 64
+  // halves; norm_h = |hi + lo|^2 / 2^2e; xh_scale (device, 1 float) = 2^-e
+  const __half* xh_hi = nullptr;
+  const __half* xh_lo = nullptr;
+  const float* norm_h = nullptr;
+  const float* xh_scale = nullptr;
 };
 
 // mu (d doubles, device) = column means of X.

@@ -262,7 +262,9 @@ int launch_grad_pw(gp_ctx* ctx, const Prep& p, const float* U, const float* W,
 int grad_tiles(gp_ctx* ctx, const Prep& p, const float* U, const float* W,
                int T1, double* G, double* gs, int precision) {
   (void)gs;   // G[d_pad] holds the outputscale sum
-  if (precision == GP_FP32_SPLIT_TF32 && grad_tc_supported(p, T1)) return grad_tc(ctx, p, U, W, T1, G);
+  // the split FP16 form keeps the TF32 split features for this kernel
+  if ((precision == GP_FP32_SPLIT_TF32 || precision == GP_FP32_SPLIT_F16) && grad_tc_supported(p, T1))
+    return grad_tc(ctx, p, U, W, T1, G);
   if (2 * T1 > 128) return set_err(ctx, GP_EINVAL, "gradient: at most 63 probes");
   switch (p.d_pad) {
     case 32: return launch_grad_pw<32>(ctx, p, U, W, T1, G);

@@ -1,4 +1,5 @@
-// Tensor-core K-hat V on sm_103a (tcgen05 + TMEM + TMA), split-TF32.
+// Tensor-core K-hat V on sm_103a (tcgen05 + TMEM + TMA): split TF32, single
+// TF32, and split FP16 (kind::f16, power-of-two scaled operands).
 //
 // arXiv 2109.09817 Sec. 3.1-3.2 (blackbox products with K-hat, O(N)
 // memory) and Sec. 4 (kernel tiles).  Per CTA: a 128-row tile I and a range
@@ -43,11 +44,16 @@ constexpr int GROUP_WARPS = 8;    // one epilogue group: 2 warps per TMEM lane q
 constexpr int OGROUP = 2;         // a group's J tiles accumulated in TMEM per O drain
 
 // ------------------------------------------------------------- layout ------
-template <int DP, int T>
+// F16: operands are FP16 (2 bytes), so a 128-byte K box holds 64 elements
+// and one MMA k-step (32 bytes) covers 16 of them instead of 8.
+template <int DP, int T, bool F16 = false>
 struct TcLayout {
-  static constexpr int KB = DP / 32;                   // 128-byte K boxes of X~
+  static constexpr int ES = F16 ? 2 : 4;               // operand element bytes
+  static constexpr int BOXE = 128 / ES;                // elements per K box
+  static constexpr int KSTEP = 32 / ES;                // K elements per MMA
+  static constexpr int KB = DP / BOXE;                 // 128-byte K boxes of X~
   static constexpr int NSB = T <= 16 ? 3 : 2;          // S/K buffers in TMEM
-  static constexpr int XS = DP <= 32 ? 4 : 3;          // X~_J ring slots
+  static constexpr int XS = F16 ? 6 : (DP <= 32 ? 4 : 3);  // X~_J ring slots
   static constexpr int VS = T <= 16 ? NSB + 2 : NSB + 1;  // V_J ring slots (>= NSB)
   static constexpr int A_BOX = BM * 128;               // bytes per K box, A
   static constexpr int XJ_BOX = BN * 128;              // bytes per K box, X~_J
@@ -58,11 +64,11 @@ struct TcLayout {
   // hi and lo stack into one N = 128 B operand
   static constexpr int X_SLOT = KB * 2 * XJ_BOX;
   static constexpr int X0 = A_LO + KB * A_BOX;
-  // V_J slot: per 32-column box vb: [hi T rows][lo T rows]; then V_hi in
-  // BF16 (T rows of 64 columns = one 128-byte atom row each); then the 64
-  // column norms
+  // V_J slot, TF32: per 32-column box vb: [hi T rows][lo T rows]; then V_hi
+  // in BF16 (T rows of 64 columns = one 128-byte atom row each).  FP16: one
+  // 64-column box [hi T rows][lo T rows].  Then the 64 column norms.
   static constexpr int V_BF = 2 * 2 * V_BOX;
-  static constexpr int V_NRM = V_BF + T * 128;
+  static constexpr int V_NRM = F16 ? 2 * V_BOX : V_BF + T * 128;
   static constexpr int V_SLOT = (V_NRM + 256 + 1023) / 1024 * 1024;
   static constexpr int V0 = X0 + XS * X_SLOT;
   static constexpr int BAR = V0 + VS * V_SLOT;
@@ -70,16 +76,18 @@ struct TcLayout {
   static constexpr int TOTAL = BAR + NBAR * 8 + 16;
   static constexpr uint32_t TX_A = 2u * KB * A_BOX;
   static constexpr uint32_t TX_X = 2u * KB * XJ_BOX;
-  static constexpr uint32_t TX_V = 4u * V_BOX + T * 128u + 256u;   // split form
+  static constexpr uint32_t TX_V = F16 ? 2u * V_BOX + 256u : 4u * V_BOX + T * 128u + 256u;  // split forms
   static constexpr uint32_t TX_V1 = 2u * V_BOX + 256u;             // single TF32
   // TMEM columns
   // per S buffer b: [b*128, +64) the hi.hi product, then K_hi;
   //                 [b*128+64, +64) the hi.lo + lo.hi products, then K_lo
+  // (FP16 K_hi and K_lo, and BF16 K_lo, two per 32-bit column)
   static constexpr uint32_t T_S = 0;
   static constexpr uint32_t T_X = 64;
   static constexpr uint32_t T_O = NSB * 128;  // 2 epilogue groups x 2 x 2T: O (hh | hi.lo part)
   static constexpr uint32_t T_COLS = 512;
   static_assert(T_O + 8 * T <= T_COLS, "TMEM columns");
+  static_assert(KB >= 1 && DP % BOXE == 0, "feature width");
   // dynamic + 1024 alignment slack + 1024 static (the failure flag) <= 227 KB
   static_assert(TOTAL + 2048 <= 232448, "shared memory");
 };
@@ -95,16 +103,26 @@ struct TcParams {
   int sym;
   int tiles_per_split;
   int* status;
+  // FP16 form only (device scalars): row and column feature scales 2^-e,
+  // and per output vector the factor 2^-(e_c + 14) that undoes the scaling
+  // of V_c and of K
+  const float* xs_r;
+  const float* xs_c;
+  const float* vsc;
 };
 
-// MMA1 k-steps KK..DP/8-1 (8 tf32 = 32 B per step inside 128 B atoms).
+// MMA1 k-steps KK..NK-1 (32 B per step inside 128 B atoms: 8 TF32 or 16
+// FP16 features).
 template <class Ly, bool SPLIT, int KK, int NK>
 __device__ __forceinline__ void mma1_steps(uint32_t dhh, uint32_t dx, uint64_t dA_hi, uint64_t dA_lo, uint64_t dX,
                                            uint32_t id1w, uint32_t id1) {
   if constexpr (KK < NK) {
     constexpr uint32_t AO = ((KK >> 2) * Ly::A_BOX + (KK & 3) * 32) >> 4;
     constexpr uint32_t BO = ((KK >> 2) * 2 * Ly::XJ_BOX + (KK & 3) * 32) >> 4;
-    if constexpr (SPLIT) {
+    if constexpr (Ly::ES == 2) {
+      mma_ss_f16_imm<AO, BO>(dhh, dA_hi, dX, id1w, KK ? 1u : 0u);
+      mma_ss_f16_imm<AO, BO>(dx, dA_lo, dX, id1, 1u);
+    } else if constexpr (SPLIT) {
       mma_ss_imm<AO, BO>(dhh, dA_hi, dX, id1w, KK ? 1u : 0u);
       mma_ss_imm<AO, BO>(dx, dA_lo, dX, id1, 1u);
     } else {
@@ -140,14 +158,33 @@ __device__ __forceinline__ void mma2_lo_steps(uint32_t d, uint32_t klo, uint64_t
   }
 }
 
-// SPLIT: hi/lo products (split-TF32); otherwise one TF32 product per term.
-template <int DP, int T, bool SPLIT>
+// FP16 contraction, 16 columns per k-step: O[0, 2T) += K_hi [V_hi; V_lo]
+// (N = 2T), then O[0, T) += K_lo V_hi (N = T).  K_hi and K_lo of columns
+// [32h + 16 half, +16) sit, two FP16 per 32-bit column, in TMEM columns
+// [32h + 8 half, +8) of their regions, so k-step kk reads 8 columns at
+// (kk >> 1) * 32 + (kk & 1) * 8; B advances 32 bytes per k-step inside the
+// 128-byte rows of the V slot.
+template <class Ly, int KK, int NK>
+__device__ __forceinline__ void mma2_f16_steps(uint32_t d, uint32_t khi, uint32_t klo, uint64_t dV,
+                                               uint32_t id2w, uint32_t id2, uint32_t acc0) {
+  if constexpr (KK < NK) {
+    constexpr uint32_t AO = (KK >> 1) * 32 + (KK & 1) * 8;
+    constexpr uint32_t BO = (KK * 32) >> 4;
+    mma_ts_bf16_imm<AO, BO>(d, khi, dV, id2w, KK == 0 ? acc0 : 1u);
+    mma_ts_bf16_imm<AO, BO>(d, klo, dV, id2, 1u);
+    mma2_f16_steps<Ly, KK + 1, NK>(d, khi, klo, dV, id2w, id2, acc0);
+  }
+}
+
+// OP: 0 = single TF32, 1 = split TF32 (hi/lo products), 2 = split FP16.
+template <int DP, int T, int OP>
 __global__ void __launch_bounds__(NTHREADS, 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constant__ CUtensorMap map_r_lo,
               const __grid_constant__ CUtensorMap map_c_hi, const __grid_constant__ CUtensorMap map_c_lo,
               const __grid_constant__ CUtensorMap map_v_hi, const __grid_constant__ CUtensorMap map_v_lo,
               const __grid_constant__ CUtensorMap map_v_bf, const TcParams p) {
-  using Ly = TcLayout<DP, T>;
+  constexpr bool SPLIT = OP != 0, F16 = OP == 2;
+  using Ly = TcLayout<DP, T, F16>;
   constexpr int NSB = Ly::NSB, XS = Ly::XS, VS = Ly::VS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled tiles
@@ -214,8 +251,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
     // ------------------------------------------------------- TMA producer --
     mbar_expect_tx(bar_a, SPLIT ? Ly::TX_A : Ly::TX_A / 2);
     for (int kb = 0; kb < Ly::KB; ++kb) {
-      tma_2d(smem + Ly::A_HI + kb * Ly::A_BOX, &map_r_hi, bar_a, kb * 32, (int)row0);
-      if (SPLIT) tma_2d(smem + Ly::A_LO + kb * Ly::A_BOX, &map_r_lo, bar_a, kb * 32, (int)row0);
+      tma_2d(smem + Ly::A_HI + kb * Ly::A_BOX, &map_r_hi, bar_a, kb * Ly::BOXE, (int)row0);
+      if (SPLIT) tma_2d(smem + Ly::A_LO + kb * Ly::A_BOX, &map_r_lo, bar_a, kb * Ly::BOXE, (int)row0);
     }
     int armed = 0;   // tiles whose loads (both rings) have been issued
     for (int j = 0; j < ntiles; ++j) {
@@ -225,8 +262,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       uint8_t* xb = smem + Ly::X0 + xs * Ly::X_SLOT;
       mbar_expect_tx(bar_xf + xs, SPLIT ? Ly::TX_X : Ly::TX_X / 2);
       for (int kb = 0; kb < Ly::KB; ++kb) {
-        tma_2d(xb + (2 * kb) * Ly::XJ_BOX, &map_c_hi, bar_xf + xs, kb * 32, col0);
-        if (SPLIT) tma_2d(xb + (2 * kb + 1) * Ly::XJ_BOX, &map_c_lo, bar_xf + xs, kb * 32, col0);
+        tma_2d(xb + (2 * kb) * Ly::XJ_BOX, &map_c_hi, bar_xf + xs, kb * Ly::BOXE, col0);
+        if (SPLIT) tma_2d(xb + (2 * kb + 1) * Ly::XJ_BOX, &map_c_lo, bar_xf + xs, kb * Ly::BOXE, col0);
       }
       if (j >= VS && !mbar_wait(bar_ve + vs, ((j / VS) - 1) & 1, &fail)) {
         // the X~_J loads of this tile are in flight: let them land first
@@ -235,11 +272,16 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       }
       uint8_t* vb = smem + Ly::V0 + vs * Ly::V_SLOT;
       mbar_expect_tx(bar_vf + vs, SPLIT ? Ly::TX_V : Ly::TX_V1);
-      for (int b = 0; b < 2; ++b) {
-        tma_2d(vb + (2 * b) * Ly::V_BOX, &map_v_hi, bar_vf + vs, col0 + b * 32, 0);
-        if (SPLIT) tma_2d(vb + (2 * b + 1) * Ly::V_BOX, &map_v_lo, bar_vf + vs, col0 + b * 32, 0);
+      if constexpr (F16) {
+        tma_2d(vb, &map_v_hi, bar_vf + vs, col0, 0);
+        tma_2d(vb + Ly::V_BOX, &map_v_lo, bar_vf + vs, col0, 0);
+      } else {
+        for (int b = 0; b < 2; ++b) {
+          tma_2d(vb + (2 * b) * Ly::V_BOX, &map_v_hi, bar_vf + vs, col0 + b * 32, 0);
+          if (SPLIT) tma_2d(vb + (2 * b + 1) * Ly::V_BOX, &map_v_lo, bar_vf + vs, col0 + b * 32, 0);
+        }
+        if (SPLIT) tma_2d(vb + Ly::V_BF, &map_v_bf, bar_vf + vs, col0, 0);
       }
-      if (SPLIT) tma_2d(vb + Ly::V_BF, &map_v_bf, bar_vf + vs, col0, 0);
       bulk_g2s(vb + Ly::V_NRM, p.nc + col0, 256, bar_vf + vs);
       armed = j + 1;
     }
@@ -255,10 +297,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
     // epilogue group g = j & 1, the group's i-th tile with i = j >> 1; the
     // group's O accumulates OGROUP of its tiles in buffer u = (i / OGROUP) & 1.
     // MMA1(j) reuses buffer b only after MMA2(j - NSB) has completed.
-    constexpr uint32_t ID1 = idesc_tf32(BM, BN);          // N = 64
-    constexpr uint32_t ID1W = idesc_tf32(BM, 2 * BN);     // N = 128: [hi; lo] stacked
-    constexpr uint32_t ID2 = idesc_tf32(BM, T);
-    constexpr uint32_t ID2W = idesc_tf32(BM, 2 * T);
+    constexpr uint32_t ID1 = F16 ? idesc_f16(BM, BN) : idesc_tf32(BM, BN);            // N = 64
+    constexpr uint32_t ID1W = F16 ? idesc_f16(BM, 2 * BN) : idesc_tf32(BM, 2 * BN);   // N = 128: [hi; lo]
+    constexpr uint32_t ID2 = F16 ? idesc_f16(BM, T) : idesc_tf32(BM, T);
+    constexpr uint32_t ID2W = F16 ? idesc_f16(BM, 2 * T) : idesc_tf32(BM, 2 * T);
     constexpr uint32_t ID2B = idesc_bf16(BM, T);
     // SMEM descriptors are built once; an operand at byte offset o from a
     // 1024-aligned base has descriptor desc(base) + (o >> 4), so every MMA
@@ -280,7 +322,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       const uint64_t dX = dX0 + (uint64_t)(xs * (Ly::X_SLOT >> 4));
       const uint32_t dhh = tbase + Ly::T_S + b * 128;
       const uint32_t dx = dhh + Ly::T_X;
-      mma1_steps<Ly, SPLIT, 0, DP / 8>(dhh, dx, dA_hi, dA_lo, dX, ID1W, ID1);
+      mma1_steps<Ly, SPLIT, 0, DP / Ly::KSTEP>(dhh, dx, dA_hi, dA_lo, dX, ID1W, ID1);
       mma_commit(bar_xe + xs);
       mma_commit(bar_s + b);
       return true;
@@ -294,8 +336,12 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       const uint64_t dV = dV0 + (uint64_t)(vs * (Ly::V_SLOT >> 4));
       const uint32_t d = tbase + ocol;
       const uint32_t khi = tbase + Ly::T_S + b * 128, klo = khi + Ly::T_X;
-      mma2_steps<Ly, SPLIT, 0, BN / 8>(d, khi, klo, dV, ID2W, ID2, first ? 0u : 1u);
-      if constexpr (SPLIT) mma2_lo_steps<Ly, 0, BN / 16>(d, klo, dV + (Ly::V_BF >> 4), ID2B);
+      if constexpr (F16) {
+        mma2_f16_steps<Ly, 0, BN / 16>(d, khi, klo, dV, ID2W, ID2, first ? 0u : 1u);
+      } else {
+        mma2_steps<Ly, SPLIT, 0, BN / 8>(d, khi, klo, dV, ID2W, ID2, first ? 0u : 1u);
+        if constexpr (SPLIT) mma2_lo_steps<Ly, 0, BN / 16>(d, klo, dV + (Ly::V_BF >> 4), ID2B);
+      }
       return true;
     };
     if (warp == 1) {
@@ -337,6 +383,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
     const int r = q * 32 + lane;         // row within the tile
     const int64_t grow = row0 + r;
     const float na = p.nr[grow];
+    // u^2 = n_a + n_b + m2 S: the FP16 cross term carries the feature scales
+    const float m2 = F16 ? -2.f * p.xs_r[0] * p.xs_c[0] : -2.f;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int my_tiles = (ntiles - g + 1) / 2;   // tiles j = g, g + 2, ...
     constexpr int TH = T / 2;            // O columns drained by this warp
@@ -398,29 +446,55 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
           const float nbc = (c & 3) == 0 ? n4.x : (c & 3) == 1 ? n4.y : (c & 3) == 2 ? n4.z : n4.w;
           float sab = __uint_as_float(sh[c]);
           if (SPLIT) sab += __uint_as_float(sx[c]);
-          const float u2 = fmaxf(fmaf(-2.f, sab, na + nbc), 0.f);
+          const float u2 = fmaxf(fmaf(m2, sab, na + nbc), 0.f);
           // u = u2 / sqrt(u2) with one MUFU op; the floor keeps u2 = 0 at 0
-          const float uu = u2 * rsqrt_approx(fmaxf(u2, 1e-30f));
-          const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
-          // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder;
-          // |lo| <= 2^-11 |K|, so lo rounded to BF16 costs <= 2^-20 |K|
-          const float hi = tf32_rna(kv);
-          sh[c] = __float_as_uint(hi);
-          sx[c] = __float_as_uint(kv - hi);
+          const float rs = rsqrt_approx(fmaxf(u2, 1e-30f));
+          const float uu = u2 * rs;
+          if constexpr (F16) {
+            // 2^14 K: the scale rides in the exponent, 2^(14 - u)
+            sh[c] = __float_as_uint(fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) *
+                                    ex2_approx(fmaf(-u2, rs, (float)kKExp)));
+          } else {
+            const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
+            // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder;
+            // |lo| <= 2^-11 |K|, so lo rounded to BF16 costs <= 2^-20 |K|
+            const float hi = tf32_rna(kv);
+            sh[c] = __float_as_uint(hi);
+            sx[c] = __float_as_uint(kv - hi);
+          }
         }
         if (diag) {
-          // diagonal tile: the entry a = b is exactly k(0) = 1
+          // diagonal tile: the entry a = b is exactly k(0) = 1 (2^14 in FP16 form)
           const int64_t dc = grow - (col0 + cb);
           const uint32_t dmask = (dc >= 0 && dc < 16) ? (1u << (int)dc) : 0u;
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const bool on = (dmask >> c) & 1u;
-            sh[c] = on ? __float_as_uint(1.0f) : sh[c];
+            sh[c] = on ? __float_as_uint(F16 ? (float)(1 << kKExp) : 1.0f) : sh[c];
             sx[c] = on ? 0u : sx[c];
           }
         }
-        tmem_st16(sa, sh);
-        if (SPLIT) {
+        if constexpr (F16) {
+          // K = hi + lo to 2^-22: hi = fp16(K), lo = fp16(K - hi) (the
+          // difference is exact in FP32), two per 32-bit column (even column
+          // in the low half) over this warp's own, already read, columns
+          uint32_t hi2[8], lo2[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float a = __uint_as_float(sh[2 * i]), bb = __uint_as_float(sh[2 * i + 1]);
+            const __half2 hv = __floats2half2_rn(a, bb);
+            const float2 hf = __half22float2(hv);
+            const __half2 lv = __floats2half2_rn(a - hf.x, bb - hf.y);
+            hi2[i] = *reinterpret_cast<const uint32_t*>(&hv);
+            lo2[i] = *reinterpret_cast<const uint32_t*>(&lv);
+          }
+          const uint32_t kc = tbase + lane_off + Ly::T_S + b * 128 + h * 32 + half * 8;
+          tmem_st8(kc, hi2);
+          tmem_st8(kc + Ly::T_X, lo2);
+        } else {
+          tmem_st16(sa, sh);
+        }
+        if (SPLIT && !F16) {
           // K_lo as BF16 pairs (even column in the low half) into this warp's
           // own S_x columns, already read above: [32h + 8 half, +8)
           uint32_t lo2[8];
@@ -445,7 +519,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
 #pragma unroll
       for (int c = 0; c < TH; ++c) {
         const int col = h * TH + c;
-        if (col < p.t) atomicAdd(p.out + (int64_t)col * p.ldo + grow, p.s * (acc[c] - cmp[c]));
+        if (col < p.t)
+          atomicAdd(p.out + (int64_t)col * p.ldo + grow, p.s * (acc[c] - cmp[c]) * (F16 ? p.vsc[col] : 1.f));
       }
     }
   }
@@ -477,31 +552,78 @@ __global__ void split_v_kernel(const float* __restrict__ V, int64_t ldv, int t, 
   }
 }
 
+// Per-vector max |v| for the FP16 split: grid (blocks, t), the bits of a
+// non-negative float (integer order = float order).
+__global__ void vmax_kernel(const float* __restrict__ V, int64_t ldv, int64_t n, unsigned* __restrict__ vmax) {
+  const int c = blockIdx.y;
+  float m = 0.f;
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(V[c * ldv + a]));
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(vmax + c, __float_as_uint(m));
+}
+
+// V -> FP16 hi/lo of 2^e_c V_c, e_c putting max |V_c| into [2^14, 2^15);
+// vsc[c] = 2^-(e_c + 14) undoes that scale and the 2^14 of K.
+__global__ void split_vh_kernel(const float* __restrict__ V, int64_t ldv, int t, int64_t n, int tpad,
+                                int64_t npad, const unsigned* __restrict__ vmax, __half* __restrict__ vhi,
+                                __half* __restrict__ vlo, float* __restrict__ vsc) {
+  const int64_t total = (int64_t)tpad * npad;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / npad, a = i % npad;
+    const float m = c < t ? __uint_as_float(vmax[c]) : 0.f;
+    int e = 0;
+    if (m > 0.f) {
+      int ex;
+      frexpf(m, &ex);
+      e = kHalfTop - ex;
+    }
+    const float v = (c < t && a < n) ? ldexpf(V[c * ldv + a], e) : 0.f;
+    const __half h = __float2half_rn(v);
+    vhi[i] = h;
+    vlo[i] = __float2half_rn(v - __half2float(h));
+    if (a == 0) vsc[c] = ldexpf(1.f, -(e + kKExp));
+  }
+}
+
 // ------------------------------------------------------------- host side ----
-template <int DP, int T, bool SPLIT>
-int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi, const float* vlo,
-              const __nv_bfloat16* vbf, int64_t vld, int t, float* out, int64_t ldo, float s, bool sym,
-              bool split, int* status) {
-  using Ly = TcLayout<DP, T>;
+template <int DP, int T, int OP>
+int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const void* vhi, const void* vlo,
+              const __nv_bfloat16* vbf, const float* vsc, int64_t vld, int t, float* out, int64_t ldo, float s,
+              bool sym, int* status) {
+  constexpr bool SPLIT = OP != 0, F16 = OP == 2;
+  using Ly = TcLayout<DP, T, F16>;
   CUtensorMap mrh, mrl, mch, mcl, mvh, mvl, mvb;
-  const float* rlo = split ? rows.xt_lo : rows.xt_hi;
-  const float* clo = split ? cols.xt_lo : cols.xt_hi;
-  GP_TRY(make_map(ctx, &mrh, rows.xt_hi, rows.n_pad, DP, DP, BM));
-  GP_TRY(make_map(ctx, &mrl, rlo, rows.n_pad, DP, DP, BM));
-  GP_TRY(make_map(ctx, &mch, cols.xt_hi, cols.n_pad, DP, DP, BN));
-  GP_TRY(make_map(ctx, &mcl, clo, cols.n_pad, DP, DP, BN));
-  GP_TRY(make_map(ctx, &mvh, vhi, T, cols.n_pad, vld, T));
-  GP_TRY(make_map(ctx, &mvl, split ? vlo : vhi, T, cols.n_pad, vld, T));
-  // V_hi in BF16: boxes of 64 columns (128 bytes) x T rows
-  if (split) {
-    GP_TRY(make_map(ctx, &mvb, vbf, T, cols.n_pad, vld, T, 64, true, true));
-  } else {
+  if constexpr (F16) {
+    // 16-bit elements: 64 features (128 bytes) per box row
+    GP_TRY(make_map(ctx, &mrh, rows.xh_hi, rows.n_pad, DP, DP, BM, 64, true, true));
+    GP_TRY(make_map(ctx, &mrl, rows.xh_lo, rows.n_pad, DP, DP, BM, 64, true, true));
+    GP_TRY(make_map(ctx, &mch, cols.xh_hi, cols.n_pad, DP, DP, BN, 64, true, true));
+    GP_TRY(make_map(ctx, &mcl, cols.xh_lo, cols.n_pad, DP, DP, BN, 64, true, true));
+    GP_TRY(make_map(ctx, &mvh, vhi, T, cols.n_pad, vld, T, 64, true, true));
+    GP_TRY(make_map(ctx, &mvl, vlo, T, cols.n_pad, vld, T, 64, true, true));
     mvb = mvh;
+  } else {
+    const float* rlo = SPLIT ? rows.xt_lo : rows.xt_hi;
+    const float* clo = SPLIT ? cols.xt_lo : cols.xt_hi;
+    GP_TRY(make_map(ctx, &mrh, rows.xt_hi, rows.n_pad, DP, DP, BM));
+    GP_TRY(make_map(ctx, &mrl, rlo, rows.n_pad, DP, DP, BM));
+    GP_TRY(make_map(ctx, &mch, cols.xt_hi, cols.n_pad, DP, DP, BN));
+    GP_TRY(make_map(ctx, &mcl, clo, cols.n_pad, DP, DP, BN));
+    GP_TRY(make_map(ctx, &mvh, vhi, T, cols.n_pad, vld, T));
+    GP_TRY(make_map(ctx, &mvl, SPLIT ? vlo : vhi, T, cols.n_pad, vld, T));
+    // V_hi in BF16: boxes of 64 columns (128 bytes) x T rows
+    if (SPLIT) {
+      GP_TRY(make_map(ctx, &mvb, vbf, T, cols.n_pad, vld, T, 64, true, true));
+    } else {
+      mvb = mvh;
+    }
   }
   const size_t smem = Ly::TOTAL + 1024;
   static bool attr = false;
   if (!attr) {
-    GP_CUDA(ctx, cudaFuncSetAttribute(kmv_tc_kernel<DP, T, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GP_CUDA(ctx, cudaFuncSetAttribute(kmv_tc_kernel<DP, T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     attr = true;
   }
@@ -513,14 +635,16 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   // launch order, so every row tile finishes band y before band y + 1 starts
   // and each band of X~_J / V_J is read from DRAM about once, instead of once
   // per wave of CTAs that have drifted apart.
-  const int64_t tile_bytes = (int64_t)BN * (DP + T) * 4 * (SPLIT ? 2 : 1) + (SPLIT ? (int64_t)BN * T * 2 : 0) + 256;
+  const int64_t tile_bytes =
+      F16 ? (int64_t)BN * (DP + T) * 2 * 2 + 256
+          : (int64_t)BN * (DP + T) * 4 * (SPLIT ? 2 : 1) + (SPLIT ? (int64_t)BN * T * 2 : 0) + 256;
   const int64_t band_tiles = std::max<int64_t>(64, (48LL << 20) / tile_bytes);
   splits = std::max<int64_t>(splits, ceil_div(col_tiles, band_tiles));
   const int64_t per = ceil_div(col_tiles, splits);
   splits = ceil_div(col_tiles, per);
   TcParams prm;
-  prm.nr = rows.norm;
-  prm.nc = cols.norm;
+  prm.nr = F16 ? rows.norm_h : rows.norm;
+  prm.nc = F16 ? cols.norm_h : cols.norm;
   prm.nrows = rows.n;
   prm.ncols = cols.n;
   prm.out = out;
@@ -530,7 +654,10 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
   prm.sym = sym ? 1 : 0;
   prm.tiles_per_split = (int)per;
   prm.status = status;
-  kmv_tc_kernel<DP, T, SPLIT><<<dim3((unsigned)row_tiles, (unsigned)splits), NTHREADS, smem, ctx->stream>>>(
+  prm.xs_r = rows.xh_scale;
+  prm.xs_c = cols.xh_scale;
+  prm.vsc = vsc;
+  kmv_tc_kernel<DP, T, OP><<<dim3((unsigned)row_tiles, (unsigned)splits), NTHREADS, smem, ctx->stream>>>(
       mrh, mrl, mch, mcl, mvh, mvl, mvb, prm);
   GP_LAUNCHED(ctx);
   return GP_OK;
@@ -540,6 +667,7 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* vhi,
 
 bool kmv_tc_supported(const Prep& rows, int t, int precision) {
   (void)t;
+  if (precision == GP_FP32_SPLIT_F16) return rows.xh_hi != nullptr && rows.d_pad <= kHalfCols;
   if (precision != GP_FP32_SPLIT_TF32 && precision != GP_TF32) return false;
   return rows.d_pad == 32 || rows.d_pad == 64;
 }
@@ -574,38 +702,60 @@ int check_status(gp_ctx* ctx) {
 
 int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V, int64_t ldv, int t,
            float* out, int64_t ldo, float s, bool sym, int precision) {
+  const bool f16 = precision == GP_FP32_SPLIT_F16;
   const bool split = precision == GP_FP32_SPLIT_TF32;
-  if (!rows.xt_hi || !cols.xt_hi) return set_err(ctx, GP_EINVAL, "tensor-core features not prepared");
+  if (f16 ? (!rows.xh_hi || !cols.xh_hi) : (!rows.xt_hi || !cols.xt_hi))
+    return set_err(ctx, GP_EINVAL, "tensor-core features not prepared");
   int* status = device_status(ctx);
   if (!status) return set_err(ctx, GP_ENOMEM, "workspace (status)");
   const int64_t npad = cols.n_pad;
   for (int c0 = 0; c0 < t; c0 += 32) {
     const int tc = std::min(32, t - c0);
     const int T = tc <= 16 ? 16 : 32;
+    const int64_t total = (int64_t)T * npad;
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 16LL * ctx->num_sms);
+    const float* Vc = V + (int64_t)c0 * ldv;
+    float* oc = out + (int64_t)c0 * ldo;
+    int rc;
+    if (f16) {
+      __half* vhi = ws<__half>(ctx, WS_VHI, (size_t)T * npad);
+      __half* vlo = ws<__half>(ctx, WS_VLO, (size_t)T * npad);
+      unsigned* vmax = ws<unsigned>(ctx, WS_VMAX, 64);   // [0, 32) max bits, [32, 64) vsc
+      if (!vhi || !vlo || !vmax) return set_err(ctx, GP_ENOMEM, "workspace (V split)");
+      float* vsc = reinterpret_cast<float*>(vmax + 32);
+      GP_CUDA(ctx, cudaMemsetAsync(vmax, 0, sizeof(unsigned) * 32, ctx->stream));
+      const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cols.n, 1024), 2LL * ctx->num_sms));
+      vmax_kernel<<<dim3(gb, (unsigned)tc), 256, 0, ctx->stream>>>(Vc, ldv, cols.n, vmax);
+      GP_LAUNCHED(ctx);
+      split_vh_kernel<<<g, 256, 0, ctx->stream>>>(Vc, ldv, tc, cols.n, T, npad, vmax, vhi, vlo, vsc);
+      GP_LAUNCHED(ctx);
+      rc = T == 16 ? launch_tc<kHalfCols, 16, 2>(ctx, rows, cols, vhi, vlo, nullptr, vsc, npad, tc, oc, ldo, s,
+                                                 sym, status)
+                   : launch_tc<kHalfCols, 32, 2>(ctx, rows, cols, vhi, vlo, nullptr, vsc, npad, tc, oc, ldo, s,
+                                                 sym, status);
+      if (rc != GP_OK) return rc;
+      continue;
+    }
     float* vhi = ws<float>(ctx, WS_VHI, (size_t)T * npad);
     float* vlo = ws<float>(ctx, WS_VLO, (size_t)T * npad);
     __nv_bfloat16* vbf = split ? ws<__nv_bfloat16>(ctx, WS_VBHI, (size_t)T * npad) : nullptr;
     if (!vhi || !vlo || (split && !vbf)) return set_err(ctx, GP_ENOMEM, "workspace (V split)");
-    const int64_t total = (int64_t)T * npad;
-    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 16LL * ctx->num_sms);
-    split_v_kernel<<<g, 256, 0, ctx->stream>>>(V + (int64_t)c0 * ldv, ldv, tc, cols.n, T, npad, vhi, vlo, vbf);
+    split_v_kernel<<<g, 256, 0, ctx->stream>>>(Vc, ldv, tc, cols.n, T, npad, vhi, vlo, vbf);
     GP_LAUNCHED(ctx);
-    float* oc = out + (int64_t)c0 * ldo;
-    int rc;
     if (split) {
       if (rows.d_pad == 32)
-        rc = T == 16 ? launch_tc<32, 16, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status)
-                     : launch_tc<32, 32, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status);
+        rc = T == 16 ? launch_tc<32, 16, 1>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status)
+                     : launch_tc<32, 32, 1>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status);
       else
-        rc = T == 16 ? launch_tc<64, 16, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status)
-                     : launch_tc<64, 32, true>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, true, status);
+        rc = T == 16 ? launch_tc<64, 16, 1>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status)
+                     : launch_tc<64, 32, 1>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status);
     } else {
       if (rows.d_pad == 32)
-        rc = T == 16 ? launch_tc<32, 16, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status)
-                     : launch_tc<32, 32, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status);
+        rc = T == 16 ? launch_tc<32, 16, 0>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status)
+                     : launch_tc<32, 32, 0>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status);
       else
-        rc = T == 16 ? launch_tc<64, 16, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status)
-                     : launch_tc<64, 32, false>(ctx, rows, cols, vhi, vlo, vbf, npad, tc, oc, ldo, s, sym, false, status);
+        rc = T == 16 ? launch_tc<64, 16, 0>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status)
+                     : launch_tc<64, 32, 0>(ctx, rows, cols, vhi, vlo, vbf, nullptr, npad, tc, oc, ldo, s, sym, status);
     }
     if (rc != GP_OK) return rc;
   }

@@ -1,5 +1,5 @@
 // Feature preparation (A1): column means, scaled/centred features, row
-// norms and the split (hi + lo) copies the tensor-core product reads.
+// norms and the split (hi + lo) copies the tensor-core products read.
 //
 // Kernel definition (arXiv 2109.09817, Sec. 4 "Matern 5/2"; ARD reading):
 // r^2 = sum_j ((x_j - x'_j)/l_j)^2 is translation invariant, so the features
@@ -48,19 +48,20 @@ __global__ void mean_final_kernel(const double* __restrict__ part, int nblk,
 }
 
 // One warp per (padded) row.  norm_mode: 0 = |x~|^2, 1 = |hi+lo|^2 (split),
-// 2 = |hi_tf32|^2, 3 = |hi_bf16|^2, 4 = |hi+lo|^2 with bf16 parts.
+// 2 = |hi_tf32|^2.  amax (nullable): running max |x~| over the matrix, as
+// the bits of a non-negative float (their integer order is the float order).
 __global__ void prep_kernel(const float* __restrict__ X, int64_t n, int d,
                             int64_t n_pad, int d_pad,
                             const double* __restrict__ mu,
                             const double* __restrict__ scale,
                             float* __restrict__ xt, float* __restrict__ norm,
                             float* __restrict__ xhi, float* __restrict__ xlo,
-                            __nv_bfloat16* __restrict__ bhi,
-                            __nv_bfloat16* __restrict__ blo, int norm_mode) {
+                            unsigned* __restrict__ amax, int norm_mode) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= n_pad) return;
   double nrm = 0.0;
+  float vmax = 0.f;
   for (int j = lane; j < d_pad; j += 32) {
     float v = 0.f;
     if (row < n && j < d)
@@ -76,18 +77,53 @@ __global__ void prep_kernel(const float* __restrict__ X, int64_t n, int d,
       if (norm_mode == 1) e = (double)h + (double)l;
       if (norm_mode == 2) e = (double)h;
     }
-    if (bhi) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-      bhi[o] = h;
-      blo[o] = l;
-      if (norm_mode == 3) e = (double)__bfloat162float(h);
-      if (norm_mode == 4) e = (double)__bfloat162float(h) + (double)__bfloat162float(l);
-    }
+    vmax = fmaxf(vmax, fabsf(v));
     nrm += e * e;
   }
+  for (int off = 16; off > 0; off >>= 1) {
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+  }
+  if (lane == 0) {
+    norm[row] = (float)nrm;
+    if (amax && vmax > 0.f) atomicMax(amax, __float_as_uint(vmax));
+  }
+}
+
+// 2^e with e chosen so that m 2^e lies in [2^14, 2^15) (1 for m = 0).
+__device__ __forceinline__ int half_exponent(float m) {
+  if (!(m > 0.f)) return 0;
+  int ex;
+  frexpf(m, &ex);            // m = f 2^ex, f in [0.5, 1)
+  return kHalfTop - ex;
+}
+
+// FP16 split of the prepared features (GP_FP32_SPLIT_F16): one warp per
+// padded row, two of the kHalfCols columns per lane.  v' = 2^e x~ (exact),
+// hi = fp16(v'), lo = fp16(v' - hi), so hi + lo = v' to 2^-22 relative (the
+// same 22 bits as the TF32 split).  norm_h = |hi + lo|^2 2^-2e in FP64, so
+// that u^2 = n_a + n_b - 2 x~_a.x~_b vanishes for a row against itself.
+__global__ void split_h_kernel(const float* __restrict__ xt, int64_t n_pad, int d_pad,
+                               const unsigned* __restrict__ amax, __half* __restrict__ hhi,
+                               __half* __restrict__ hlo, float* __restrict__ norm_h,
+                               float* __restrict__ xh_scale) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  const int e = half_exponent(__uint_as_float(*amax));
+  if (row == 0 && lane == 0) xh_scale[0] = ldexpf(1.f, -e);
+  if (row >= n_pad) return;
+  double nrm = 0.0;
+  for (int j = lane; j < kHalfCols; j += 32) {
+    const float v = j < d_pad ? ldexpf(xt[row * d_pad + j], e) : 0.f;
+    const __half h = __float2half_rn(v);
+    const __half l = __float2half_rn(v - __half2float(h));
+    hhi[row * kHalfCols + j] = h;
+    hlo[row * kHalfCols + j] = l;
+    const double r = ldexp((double)__half2float(h) + (double)__half2float(l), -e);
+    nrm += r * r;
+  }
   for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-  if (lane == 0) norm[row] = (float)nrm;
+  if (lane == 0) norm_h[row] = (float)nrm;
 }
 
 }  // namespace
@@ -119,18 +155,29 @@ int prepare_features(gp_ctx* ctx, const float* X, int64_t n, int d,
   float* nrm = ws<float>(ctx, WS_NORM + off, (size_t)p.n_pad);
   if (!xt || !nrm) return set_err(ctx, GP_ENOMEM, "workspace (features)");
   float *xhi = nullptr, *xlo = nullptr;
-  __nv_bfloat16 *bhi = nullptr, *blo = nullptr;
   int norm_mode = 0;
-  if (precision == GP_FP32_SPLIT_TF32 || precision == GP_TF32) {
+  // the FP16 split form keeps the TF32 split too: the backward kernel of the
+  // training pass reads it
+  const bool half = precision == GP_FP32_SPLIT_F16;
+  if (precision == GP_FP32_SPLIT_TF32 || precision == GP_TF32 || half) {
     xhi = ws<float>(ctx, WS_XT_HI + off, ne);
     xlo = ws<float>(ctx, WS_XT_LO + off, ne);
     if (!xhi || !xlo) return set_err(ctx, GP_ENOMEM, "workspace (tf32 split)");
     norm_mode = precision == GP_TF32 ? 2 : 1;
-  } else if (precision == GP_BF16_SPLIT || precision == GP_BF16) {
-    bhi = ws<__nv_bfloat16>(ctx, WS_XB_HI + off, ne);
-    blo = ws<__nv_bfloat16>(ctx, WS_XB_LO + off, ne);
-    if (!bhi || !blo) return set_err(ctx, GP_ENOMEM, "workspace (bf16 split)");
-    norm_mode = precision == GP_BF16 ? 3 : 4;
+  }
+  __half *hhi = nullptr, *hlo = nullptr;
+  float *nrm_h = nullptr, *hsc = nullptr;
+  unsigned* amax = nullptr;
+  if (half) {
+    if (p.d_pad > kHalfCols) return set_err(ctx, GP_EINVAL, "split FP16 form needs d <= %d", kHalfCols);
+    const size_t nh = (size_t)p.n_pad * kHalfCols;
+    hhi = ws<__half>(ctx, WS_XH_HI + off, nh);
+    hlo = ws<__half>(ctx, WS_XH_LO + off, nh);
+    nrm_h = ws<float>(ctx, WS_NORMH + off, (size_t)p.n_pad);
+    hsc = ws<float>(ctx, WS_XH_SC + off, 64);   // [0] 2^-e, [16] max |x~| bits
+    if (!hhi || !hlo || !nrm_h || !hsc) return set_err(ctx, GP_ENOMEM, "workspace (fp16 split)");
+    amax = reinterpret_cast<unsigned*>(hsc + 16);
+    GP_CUDA(ctx, cudaMemsetAsync(amax, 0, sizeof(unsigned), ctx->stream));
   }
   // scale_j = sqrt5 log2e / l_j, staged through the pinned buffer
   // WS_SCALE is shared by both feature families; every use is stream-ordered
@@ -147,14 +194,21 @@ int prepare_features(gp_ctx* ctx, const float* X, int64_t n, int d,
   const int rows_per_block = 8;
   const unsigned grid = (unsigned)ceil_div(p.n_pad, rows_per_block);
   prep_kernel<<<grid, 32 * rows_per_block, 0, ctx->stream>>>(
-      X, n, d, p.n_pad, p.d_pad, mu_dev, scale_dev, xt, nrm, xhi, xlo, bhi, blo, norm_mode);
+      X, n, d, p.n_pad, p.d_pad, mu_dev, scale_dev, xt, nrm, xhi, xlo, amax, norm_mode);
   GP_LAUNCHED(ctx);
+  if (half) {
+    split_h_kernel<<<grid, 32 * rows_per_block, 0, ctx->stream>>>(xt, p.n_pad, p.d_pad, amax, hhi, hlo,
+                                                                    nrm_h, hsc);
+    GP_LAUNCHED(ctx);
+  }
   p.xt = xt;
   p.norm = nrm;
   p.xt_hi = xhi;
   p.xt_lo = xlo;
-  p.xb_hi = bhi;
-  p.xb_lo = blo;
+  p.xh_hi = hhi;
+  p.xh_lo = hlo;
+  p.norm_h = nrm_h;
+  p.xh_scale = hsc;
   *out = p;
   return GP_OK;
 }

@@ -85,6 +85,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor: kind::f16 with FP16 A and B, D = F32, K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 // Instruction descriptor: kind::tf32, D = F32, A and B K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -99,6 +103,17 @@ __device__ __forceinline__ void mma_ss_imm(uint32_t d, uint64_t a, uint64_t b, u
       "{\n .reg .pred p;\n .reg .b64 da, db;\n add.s64 da, %1, %5;\n add.s64 db, %2, %6;\n"
       " setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc), "n"(AO), "n"(BO)
+      : "memory");
+}
+// kind::f16 (FP16 or BF16 operands, as the instruction descriptor says), A
+// and B from SMEM.
+template <uint32_t AO, uint32_t BO>
+__device__ __forceinline__ void mma_ss_f16_imm(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n add.s64 da, %1, %5;\n add.s64 db, %2, %6;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc), "n"(AO), "n"(BO)
       : "memory");
 }
