@@ -19,7 +19,7 @@
 namespace gp {
 namespace {
 
-constexpr int kRedBlocks = 128;   // row chunks of the two-stage reductions
+constexpr int kRedBlocks = 304;   // row chunks of the two-stage reductions (2 per SM)
 
 struct CgScal {
   double rz, rz_new, dw, bnorm, relres, alpha, beta;
@@ -216,41 +216,62 @@ __global__ void z_apply_kernel(const float* __restrict__ L32, int64_t ldl, int k
 // sigma^2 = 1e-4); both row passes therefore run in FP64 from the FP64 factor
 // L (row j contiguous, ld n) and dh64.
 //
-// part[(b * k + j) * t + c] = sum over rows of block b of L[j] dh^2 R_c
-// grid (blocks, k, ceil(t / 32)), 256 threads
-__global__ void ltr64_kernel(const double* __restrict__ L, int64_t ldl, int k, const float* __restrict__ R,
-                             int64_t ldr, int t, int64_t n, const CgScal* __restrict__ sc,
-                             const double* __restrict__ dh, double* __restrict__ part) {
-  __shared__ double red[8][32];
-  const int j = blockIdx.y, c0 = blockIdx.z * 32;
-  const int nc = min(32, t - c0);
-  const double* lj = L + (int64_t)j * ldl;
-  double acc[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-  for (int64_t a = r0 + threadIdx.x; a < r1; a += blockDim.x) {
-    const double d = dh[a];
-    const double l = lj[a] * d * d;
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < nc) acc[c] += l * (double)R[(int64_t)(c0 + c) * ldr + a];
-  }
+// part[(b * k + j) * t + c] = sum over rows of block b of L[j] dh^2 R_c, a
+// k x 64-row by 64-row x t product per staged tile.  grid (blocks,
+// ceil(k / 64), ceil(t / CW)), 256 threads: lane l of warp w owns column
+// c0 + l % CW and the pivot rows j0 + (32 / CW) w + l / CW + 8 (32 / CW) m,
+// so each block reads its rows of R once per 64 pivot rows and every FMA is
+// a useful one (CW = 16 for t <= 16).
+template <int CW>
+__global__ void __launch_bounds__(256) ltr64_kernel(const double* __restrict__ L, int64_t ldl, int k,
+                                                    const float* __restrict__ R, int64_t ldr, int t, int64_t n,
+                                                    const CgScal* __restrict__ sc, const double* __restrict__ dh,
+                                                    double* __restrict__ part) {
+  constexpr int JPW = 32 / CW;          // pivot rows per warp and step
+  constexpr int M = 64 / (8 * JPW);     // accumulators per thread
+  __shared__ double Rs[32][CW + 1];     // [row][column], dh^2 folded in
+  __shared__ double Ls[64][33];         // [pivot row][row]
+  const int j0 = blockIdx.y * 64, c0 = blockIdx.z * CW;
+  const int nc = min(CW, t - c0), nj = min(64, k - j0);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cl = lane % CW, jl = w * JPW + lane / CW;
+  double acc[M];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    double v = acc[c];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) red[w][c] = v;
+  for (int m = 0; m < M; ++m) acc[m] = 0.0;
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  for (int64_t a0 = r0; a0 < r1; a0 += 32) {
+    for (int idx = threadIdx.x; idx < 32 * CW; idx += 256) {
+      const int cc = idx >> 5, aa = idx & 31;
+      const int64_t a = a0 + aa;
+      double v = 0.0;
+      if (cc < nc && a < r1) {
+        const double d = dh[a];
+        v = (double)R[(int64_t)(c0 + cc) * ldr + a] * d * d;
+      }
+      Rs[aa][cc] = v;
+    }
+    for (int idx = threadIdx.x; idx < 64 * 32; idx += 256) {
+      const int jj = idx >> 5, aa = idx & 31;
+      const int64_t a = a0 + aa;
+      Ls[jj][aa] = (jj < nj && a < r1) ? L[(int64_t)(j0 + jj) * ldl + a] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int aa = 0; aa < 32; ++aa) {
+      const double r = Rs[aa][cl];
+#pragma unroll
+      for (int m = 0; m < M; ++m) acc[m] = fma(Ls[jl + 8 * JPW * m][aa], r, acc[m]);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x < nc) {
-    double v = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
-    const int c = c0 + threadIdx.x;
-    if (sc && !sc[c].active) v = 0.0;
-    part[((int64_t)blockIdx.x * k + j) * t + c] = v;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = j0 + jl + 8 * JPW * m;
+    if (j < k && cl < nc) {
+      const int c = c0 + cl;
+      part[((int64_t)blockIdx.x * k + j) * t + c] = (sc && !sc[c].active) ? 0.0 : acc[m];
+    }
   }
 }
 
@@ -265,53 +286,60 @@ __global__ void w64_apply_kernel(const double* __restrict__ Cinv, const double* 
   w[idx] = s;
 }
 
-// Z_c = dh o (dh o R_c - sum_j dh L_j w_jc) in FP64 on 32-column chunks, rz partials
-__global__ void z64_apply_kernel(const double* __restrict__ L, int64_t ldl, int k,
+// Z_c = dh o (dh o R_c - dh o sum_j L_j w_jc) in FP64 on NC-column chunks
+// (NC = 16 for t <= 16), rz partials.  One row per thread, the k x NC chunk
+// of w in shared memory (broadcast reads).
+template <int NC>
+__global__ void __launch_bounds__(256, NC == 16 ? 2 : 1) z64_apply_kernel(const double* __restrict__ L, int64_t ldl, int k,
                                  const double* __restrict__ w, int t, const float* __restrict__ R,
                                  float* __restrict__ Z, int64_t ld, int64_t n, const double* __restrict__ dh,
                                  const CgScal* __restrict__ sc, double* __restrict__ rzpart) {
-  extern __shared__ double sw64[];   // k x 32 chunk of w
+  extern __shared__ double sw64[];   // k x NC chunk of w
   __shared__ double sh[32];
-  const int c0 = blockIdx.y * 32;
-  const int nc = min(32, t - c0);
-  for (int idx = threadIdx.x; idx < k * 32; idx += blockDim.x) {
-    const int j = idx / 32, cc = idx % 32;
+  const int c0 = blockIdx.y * NC;
+  const int nc = min(NC, t - c0);
+  for (int idx = threadIdx.x; idx < k * NC; idx += blockDim.x) {
+    const int j = idx / NC, cc = idx % NC;
     sw64[idx] = cc < nc ? w[j * t + c0 + cc] : 0.0;
   }
   __syncthreads();
-  bool act[32];
+  bool act[NC];
 #pragma unroll
-  for (int cc = 0; cc < 32; ++cc) act[cc] = cc < nc && (!sc || sc[c0 + cc].active);
+  for (int cc = 0; cc < NC; ++cc) act[cc] = cc < nc && (!sc || sc[c0 + cc].active);
   const int nblk = gridDim.x;
   const int64_t chunk = (n + nblk - 1) / nblk;
   const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-  double rz[32];
+  double rz[NC];
 #pragma unroll
-  for (int cc = 0; cc < 32; ++cc) rz[cc] = 0.0;
+  for (int cc = 0; cc < NC; ++cc) rz[cc] = 0.0;
   for (int64_t a = r0 + threadIdx.x; a < r1; a += blockDim.x) {
     const double d = dh[a];
-    double acc[32];
+    double acc[NC];
 #pragma unroll
-    for (int cc = 0; cc < 32; ++cc) acc[cc] = 0.0;
+    for (int cc = 0; cc < NC; ++cc) acc[cc] = 0.0;
     for (int j = 0; j < k; ++j) {
-      const double l = L[(int64_t)j * ldl + a] * d;
+      const double l = L[(int64_t)j * ldl + a];
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc) acc[cc] = fma(l, sw64[j * 32 + cc], acc[cc]);
+      for (int cc = 0; cc < NC; ++cc) acc[cc] = fma(l, sw64[j * NC + cc], acc[cc]);
     }
 #pragma unroll
-    for (int cc = 0; cc < 32; ++cc) {
+    for (int cc = 0; cc < NC; ++cc) {
       if (!act[cc]) continue;
       const int64_t o = (int64_t)(c0 + cc) * ld + a;
       const float r = R[o];
-      const double z = d * fma(d, (double)r, -acc[cc]);
+      const double z = d * d * ((double)r - acc[cc]);
       Z[o] = (float)z;
       rz[cc] += (double)r * z;
     }
   }
   if (rzpart) {
-    for (int cc = 0; cc < nc; ++cc) {
-      const double v = block_sum(rz[cc], sh);
-      if (threadIdx.x == 0) rzpart[(int64_t)(c0 + cc) * nblk + blockIdx.x] = v;
+    // unrolled with a block-uniform guard, so that rz stays in registers
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+      if (cc < nc) {
+        const double v = block_sum(rz[cc], sh);
+        if (threadIdx.x == 0) rzpart[(int64_t)(c0 + cc) * nblk + blockIdx.x] = v;
+      }
     }
   }
 }
@@ -546,19 +574,33 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
     double* w64 = ws<double>(ctx, WS_CG_W64, (size_t)k * t);
     if (!part || !w64) return set_err(ctx, GP_ENOMEM, "workspace (precond)");
     double* G = part + (size_t)nb * k * t;
-    ltr64_kernel<<<dim3(nb, k, (unsigned)ceil_div(t, 32)), 256, 0, ctx->stream>>>(pc->L, pc->n, k, R, ld, t, n, sc,
-                                                                                 pc->dh64, part);
+    if (t <= 16)
+      ltr64_kernel<16><<<dim3(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 16)), 256, 0, ctx->stream>>>(
+          pc->L, pc->n, k, R, ld, t, n, sc, pc->dh64, part);
+    else
+      ltr64_kernel<32><<<dim3(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 32)), 256, 0, ctx->stream>>>(
+          pc->L, pc->n, k, R, ld, t, n, sc, pc->dh64, part);
     GP_LAUNCHED(ctx);
     const unsigned g2 = (unsigned)ceil_div((int64_t)k * t, 128);
     g_reduce_kernel<<<g2, 128, 0, ctx->stream>>>(part, nb, k, t, sc, G);
     GP_LAUNCHED(ctx);
     w64_apply_kernel<<<g2, 128, 0, ctx->stream>>>(pc->cinv, G, k, t, w64);
     GP_LAUNCHED(ctx);
-    const size_t shm = sizeof(double) * (size_t)k * 32;
-    if (shm > 48 * 1024)
-      GP_CUDA(ctx, cudaFuncSetAttribute(z64_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    z64_apply_kernel<<<dim3(kRedBlocks, (unsigned)ceil_div(t, 32)), 256, shm, ctx->stream>>>(
-        pc->L, pc->n, k, w64, t, R, Z, ld, n, pc->dh64, sc, rzpart);
+    if (t <= 16) {
+      const size_t shm = sizeof(double) * (size_t)k * 16;
+      if (shm > 48 * 1024)
+        GP_CUDA(ctx, cudaFuncSetAttribute(z64_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shm));
+      z64_apply_kernel<16><<<dim3(kRedBlocks, 1), 256, shm, ctx->stream>>>(pc->L, pc->n, k, w64, t, R, Z, ld, n,
+                                                                         pc->dh64, sc, rzpart);
+    } else {
+      const size_t shm = sizeof(double) * (size_t)k * 32;
+      if (shm > 48 * 1024)
+        GP_CUDA(ctx, cudaFuncSetAttribute(z64_apply_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shm));
+      z64_apply_kernel<32><<<dim3(kRedBlocks, (unsigned)ceil_div(t, 32)), 256, shm, ctx->stream>>>(
+          pc->L, pc->n, k, w64, t, R, Z, ld, n, pc->dh64, sc, rzpart);
+    }
     GP_LAUNCHED(ctx);
     return GP_OK;
   }
