@@ -39,7 +39,7 @@ WORKLOADS = {
     "gp64k": ("gp64k", 31, 64, 1e-4, 1500, "sigma"),
     "gp2k": ("gp2k", 15, 32, 1e-6, 1000, "sigma"),
 }
-# K-hat products one solve of each workload needs (split-TF32 path, seed 0);
+# K-hat products one solve of each workload needs (split forms, seed 0);
 # the reference arm scales its per-product oracle time by this count.
 PRODUCTS_PER_SOLVE = {"gp1m": 97, "gp256k": 120, "gp64k": 1200, "gp2k": 60}
 # DRAM bytes (read + write) per launch of the fused tensor-core K-hat V kernel
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gp1m", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="split_tf32",
+    ap.add_argument("--precision", default="split_f16",
                     choices=["fp32", "split_tf32", "split_f16", "tf32"])
     ap.add_argument("--precond", default="auto", choices=["auto", "sigma", "resid"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

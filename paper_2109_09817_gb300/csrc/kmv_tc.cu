@@ -4,24 +4,28 @@
 // arXiv 2109.09817 Sec. 3.1-3.2 (blackbox products with K-hat, O(N)
 // memory) and Sec. 4 (kernel tiles).  Per CTA: a 128-row tile I and a range
 // of 64-column tiles J.  Per J tile:
-//   MMA1  S = X~_I X~_J^T          tcgen05.mma kind::tf32, operands in 128B-
-//                                  swizzled SMEM (TMA), accumulator in TMEM;
-//                                  split: S = hi.hi^T + hi.lo^T + lo.hi^T
+//   MMA1  S = X~_I X~_J^T          operands in 128B-swizzled SMEM (TMA),
+//                                  accumulator in TMEM; split forms:
+//                                  S = hi.hi^T + hi.lo^T + lo.hi^T
+//         TF32: hi.[hi; lo]^T as one N = 128 MMA plus lo.hi^T, two 64-column
+//         accumulators; FP16: three N = 64 MMAs into one accumulator (16
+//         features per MMA)
 //   epi   K = matern(n_a + n_b - 2S) on the FP32/MUFU pipes (8 warps), written
-//         back to TMEM as K_hi (over S) and K_lo = tf32(K - K_hi)
-//   MMA2  O_J = K_hi [V_hi V_lo] (kind::tf32) + K_lo V_hi (kind::f16, BF16
-//         operands: K_lo is 2^-11 of K, so BF16 keeps the term to 2^-20 of
-//         K V and covers 16 columns per MMA instead of 8); A from TMEM
+//         back to TMEM over S as hi + lo parts (TF32 hi and BF16 lo, or FP16
+//         hi and lo of 2^14 K)
+//   MMA2  O_J = K_hi [V_hi V_lo] + K_lo V_hi, A from TMEM.  TF32 form: the
+//         first term kind::tf32, the second kind::f16 with BF16 operands
+//         (K_lo is 2^-11 of K, so BF16 keeps the term to 2^-20 of K V and
+//         covers 16 columns per MMA instead of 8).  FP16 form: both kind::f16
 //   epi   O_J drained from TMEM and added into per-thread registers with a
 //         compensated (Kahan) sum; flushed once per CTA with atomics.
 // The tensor pipe loses roughly 500 cycles whenever it drains, so MMA1 runs
-// NSB tiles ahead of MMA2: S/K lives in NSB TMEM buffers (3 when the O
-// accumulators leave room, else 2), and MMA1 and MMA2 are issued by two
-// threads so that a wait in one does not starve the pipe.  X~_J tiles and
-// V_J tiles travel in separate TMA rings, so an X~_J slot is recycled as soon
-// as its MMA1 has run.  Warp roles: 0 TMA producer, 1 MMA1 issuer, 2 TMEM
-// allocator, 3 MMA2 issuer, 4..19 epilogue in two groups of 8 (group g takes
-// tiles j with j % 2 == g).
+// NSB tiles ahead of MMA2: S/K lives in NSB TMEM buffers, and MMA1 and MMA2
+// are issued by two threads so that a wait in one does not starve the pipe.
+// X~_J tiles and V_J tiles travel in separate TMA rings, so an X~_J slot is
+// recycled as soon as its MMA1 has run.  Warp roles: 0 TMA producer, 1 MMA1
+// issuer, 2 TMEM allocator, 3 MMA2 issuer, 4..19 epilogue in two groups of 8
+// (group g takes tiles j with j % 2 == g).
 // Every mbarrier wait is bounded: on a timeout the kernel records
 // GP_ETIMEOUT in a status word and all roles leave their loops.
 #include <cuda.h>
@@ -52,7 +56,10 @@ struct TcLayout {
   static constexpr int BOXE = 128 / ES;                // elements per K box
   static constexpr int KSTEP = 32 / ES;                // K elements per MMA
   static constexpr int KB = DP / BOXE;                 // 128-byte K boxes of X~
-  static constexpr int NSB = T <= 16 ? 3 : 2;          // S/K buffers in TMEM
+  // FP16: the three split products accumulate into one 64-column S buffer;
+  // TF32: hi.hi and the two cross products in two 64-column halves
+  static constexpr uint32_t SBW = F16 ? 64 : 128;      // TMEM columns per S/K buffer
+  static constexpr int NSB = F16 ? 4 : (T <= 16 ? 3 : 2);  // S/K buffers in TMEM
   static constexpr int XS = F16 ? 6 : (DP <= 32 ? 4 : 3);  // X~_J ring slots
   static constexpr int VS = T <= 16 ? NSB + 2 : NSB + 1;  // V_J ring slots (>= NSB)
   static constexpr int A_BOX = BM * 128;               // bytes per K box, A
@@ -84,7 +91,7 @@ struct TcLayout {
   // (FP16 K_hi and K_lo, and BF16 K_lo, two per 32-bit column)
   static constexpr uint32_t T_S = 0;
   static constexpr uint32_t T_X = 64;
-  static constexpr uint32_t T_O = NSB * 128;  // 2 epilogue groups x 2 x 2T: O (hh | hi.lo part)
+  static constexpr uint32_t T_O = NSB * SBW;  // 2 epilogue groups x 2 x 2T: O (hh | hi.lo part)
   static constexpr uint32_t T_COLS = 512;
   static_assert(T_O + 8 * T <= T_COLS, "TMEM columns");
   static_assert(KB >= 1 && DP % BOXE == 0, "feature width");
@@ -111,18 +118,15 @@ struct TcParams {
   const float* vsc;
 };
 
-// MMA1 k-steps KK..NK-1 (32 B per step inside 128 B atoms: 8 TF32 or 16
-// FP16 features).
+// MMA1 k-steps KK..NK-1 of the TF32 forms (8 features = 32 B per step
+// inside 128 B atoms).
 template <class Ly, bool SPLIT, int KK, int NK>
 __device__ __forceinline__ void mma1_steps(uint32_t dhh, uint32_t dx, uint64_t dA_hi, uint64_t dA_lo, uint64_t dX,
                                            uint32_t id1w, uint32_t id1) {
   if constexpr (KK < NK) {
     constexpr uint32_t AO = ((KK >> 2) * Ly::A_BOX + (KK & 3) * 32) >> 4;
     constexpr uint32_t BO = ((KK >> 2) * 2 * Ly::XJ_BOX + (KK & 3) * 32) >> 4;
-    if constexpr (Ly::ES == 2) {
-      mma_ss_f16_imm<AO, BO>(dhh, dA_hi, dX, id1w, KK ? 1u : 0u);
-      mma_ss_f16_imm<AO, BO>(dx, dA_lo, dX, id1, 1u);
-    } else if constexpr (SPLIT) {
+    if constexpr (SPLIT) {
       mma_ss_imm<AO, BO>(dhh, dA_hi, dX, id1w, KK ? 1u : 0u);
       mma_ss_imm<AO, BO>(dx, dA_lo, dX, id1, 1u);
     } else {
@@ -155,6 +159,22 @@ __device__ __forceinline__ void mma2_lo_steps(uint32_t d, uint32_t klo, uint64_t
   if constexpr (KK < NK) {
     mma_ts_bf16_imm<(KK >> 1) * 32 + (KK & 1) * 8, ((KK * 32) >> 4)>(d, klo, dVb, id, 1u);
     mma2_lo_steps<Ly, KK + 1, NK>(d, klo, dVb, id);
+  }
+}
+
+// FP16 cross term with the three split products in one accumulator:
+// S += A_hi X_hi^T + A_hi X_lo^T + A_lo X_hi^T, three N = 64 MMAs per k-step.
+template <class Ly, int KK, int NK>
+__device__ __forceinline__ void mma1_one_steps(uint32_t d, uint64_t dA_hi, uint64_t dA_lo, uint64_t dX,
+                                               uint32_t id1) {
+  if constexpr (KK < NK) {
+    constexpr uint32_t AO = ((KK >> 2) * Ly::A_BOX + (KK & 3) * 32) >> 4;
+    constexpr uint32_t BO = ((KK >> 2) * 2 * Ly::XJ_BOX + (KK & 3) * 32) >> 4;
+    constexpr uint32_t BL = BO + (Ly::XJ_BOX >> 4);
+    mma_ss_f16_imm<AO, BO>(d, dA_hi, dX, id1, KK ? 1u : 0u);
+    mma_ss_f16_imm<AO, BL>(d, dA_hi, dX, id1, 1u);
+    mma_ss_f16_imm<AO, BO>(d, dA_lo, dX, id1, 1u);
+    mma1_one_steps<Ly, KK + 1, NK>(d, dA_hi, dA_lo, dX, id1);
   }
 }
 
@@ -320,9 +340,12 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       if (!mbar_wait(bar_xf + xs, (j / XS) & 1, &fail)) return false;
       fence_after();
       const uint64_t dX = dX0 + (uint64_t)(xs * (Ly::X_SLOT >> 4));
-      const uint32_t dhh = tbase + Ly::T_S + b * 128;
+      const uint32_t dhh = tbase + Ly::T_S + b * Ly::SBW;
       const uint32_t dx = dhh + Ly::T_X;
-      mma1_steps<Ly, SPLIT, 0, DP / Ly::KSTEP>(dhh, dx, dA_hi, dA_lo, dX, ID1W, ID1);
+      if constexpr (F16)
+        mma1_one_steps<Ly, 0, DP / Ly::KSTEP>(dhh, dA_hi, dA_lo, dX, ID1);
+      else
+        mma1_steps<Ly, SPLIT, 0, DP / Ly::KSTEP>(dhh, dx, dA_hi, dA_lo, dX, ID1W, ID1);
       mma_commit(bar_xe + xs);
       mma_commit(bar_s + b);
       return true;
@@ -335,7 +358,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       fence_after();
       const uint64_t dV = dV0 + (uint64_t)(vs * (Ly::V_SLOT >> 4));
       const uint32_t d = tbase + ocol;
-      const uint32_t khi = tbase + Ly::T_S + b * 128, klo = khi + Ly::T_X;
+      const uint32_t khi = tbase + Ly::T_S + b * Ly::SBW, klo = khi + (F16 ? 16u : Ly::T_X);
       if constexpr (F16) {
         mma2_f16_steps<Ly, 0, BN / 16>(d, khi, klo, dV, ID2W, ID2, first ? 0u : 1u);
       } else {
@@ -431,11 +454,57 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       if (!(ok = mbar_wait(bar_vf + vs, (j / VS) & 1, &fail))) break;
       fence_after();
       const bool diag = p.sym && row0 < col0 + BN && col0 < row0 + BM;
+      if constexpr (F16) {
+        // All 32 of this warp's S columns at once.  K is held as 2^14 K (the
+        // scale rides in the exponent, 2^(14 - u)) and split into FP16
+        // hi = fp16(K) and lo = fp16(K - hi), K - hi being exact in FP32, so
+        // hi + lo = K to 2^-22.  They are packed two per 32-bit column (even
+        // column in the low half): K_hi of columns [32h + 16 half, +16) to
+        // [32h + 8 half, +8), K_lo 16 columns further on, both inside the
+        // columns already loaded.
+        const float4* snb = reinterpret_cast<const float4*>(smem + Ly::V0 + vs * Ly::V_SLOT + Ly::V_NRM) + h * 8;
+        const uint32_t sa = tbase + lane_off + Ly::T_S + b * Ly::SBW + h * 32;
+        uint32_t s32[32];
+        tmem_ld32(sa, s32);
+        tmem_wait_ld();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float kf[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int cc = half * 16 + c;
+            const float4 n4 = snb[cc >> 2];
+            const float nbc = (cc & 3) == 0 ? n4.x : (cc & 3) == 1 ? n4.y : (cc & 3) == 2 ? n4.z : n4.w;
+            const float u2 = fmaxf(fmaf(m2, __uint_as_float(s32[cc]), na + nbc), 1e-30f);
+            const float rs = rsqrt_approx(u2);
+            const float uu = u2 * rs;
+            kf[c] = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(fmaf(-u2, rs, (float)kKExp));
+          }
+          if (diag) {
+            const int64_t dc = grow - (col0 + h * 32 + half * 16);
+            const uint32_t dmask = (dc >= 0 && dc < 16) ? (1u << (int)dc) : 0u;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) kf[c] = ((dmask >> c) & 1u) ? (float)(1 << kKExp) : kf[c];
+          }
+          uint32_t hi2[8], lo2[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const __half2 hv = __floats2half2_rn(kf[2 * i], kf[2 * i + 1]);
+            const float2 hf = __half22float2(hv);
+            const __half2 lv = __floats2half2_rn(kf[2 * i] - hf.x, kf[2 * i + 1] - hf.y);
+            hi2[i] = *reinterpret_cast<const uint32_t*>(&hv);
+            lo2[i] = *reinterpret_cast<const uint32_t*>(&lv);
+          }
+          tmem_st8(sa + half * 8, hi2);
+          tmem_st8(sa + 16 + half * 8, lo2);
+        }
+      }
+      if constexpr (!F16) {
 #pragma unroll 1
       for (int half = 0; half < 2; ++half) {
         const int cb = h * 32 + half * 16;   // first of these 16 columns
         const float4* snb = reinterpret_cast<const float4*>(smem + Ly::V0 + vs * Ly::V_SLOT + Ly::V_NRM) + cb / 4;
-        const uint32_t sa = tbase + lane_off + Ly::T_S + b * 128 + cb;
+        const uint32_t sa = tbase + lane_off + Ly::T_S + b * Ly::SBW + cb;
         uint32_t sh[16], sx[16];
         tmem_ld16(sa, sh);
         if (SPLIT) tmem_ld16(sa + Ly::T_X, sx);
@@ -446,55 +515,31 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
           const float nbc = (c & 3) == 0 ? n4.x : (c & 3) == 1 ? n4.y : (c & 3) == 2 ? n4.z : n4.w;
           float sab = __uint_as_float(sh[c]);
           if (SPLIT) sab += __uint_as_float(sx[c]);
-          const float u2 = fmaxf(fmaf(m2, sab, na + nbc), 0.f);
-          // u = u2 / sqrt(u2) with one MUFU op; the floor keeps u2 = 0 at 0
-          const float rs = rsqrt_approx(fmaxf(u2, 1e-30f));
-          const float uu = u2 * rs;
-          if constexpr (F16) {
-            // 2^14 K: the scale rides in the exponent, 2^(14 - u)
-            sh[c] = __float_as_uint(fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) *
-                                    ex2_approx(fmaf(-u2, rs, (float)kKExp)));
-          } else {
-            const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
-            // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder;
-            // |lo| <= 2^-11 |K|, so lo rounded to BF16 costs <= 2^-20 |K|
-            const float hi = tf32_rna(kv);
-            sh[c] = __float_as_uint(hi);
-            sx[c] = __float_as_uint(kv - hi);
-          }
+          // u = u2 / sqrt(u2) with one MUFU op; one clamp serves both the
+          // rounding below zero and the rsqrt (u = 1e-15 for u2 <= 0 gives
+          // k = 1 to FP32 precision)
+          const float u2 = fmaxf(fmaf(m2, sab, na + nbc), 1e-30f);
+          const float uu = u2 * rsqrt_approx(u2);
+          const float kv = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(-uu);
+          // K = hi + lo exactly: hi = K rounded to TF32, lo the remainder;
+          // |lo| <= 2^-11 |K|, so lo rounded to BF16 costs <= 2^-20 |K|
+          const float hi = tf32_rna(kv);
+          sh[c] = __float_as_uint(hi);
+          sx[c] = __float_as_uint(kv - hi);
         }
         if (diag) {
-          // diagonal tile: the entry a = b is exactly k(0) = 1 (2^14 in FP16 form)
+          // diagonal tile: the entry a = b is exactly k(0) = 1
           const int64_t dc = grow - (col0 + cb);
           const uint32_t dmask = (dc >= 0 && dc < 16) ? (1u << (int)dc) : 0u;
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const bool on = (dmask >> c) & 1u;
-            sh[c] = on ? __float_as_uint(F16 ? (float)(1 << kKExp) : 1.0f) : sh[c];
+            sh[c] = on ? __float_as_uint(1.0f) : sh[c];
             sx[c] = on ? 0u : sx[c];
           }
         }
-        if constexpr (F16) {
-          // K = hi + lo to 2^-22: hi = fp16(K), lo = fp16(K - hi) (the
-          // difference is exact in FP32), two per 32-bit column (even column
-          // in the low half) over this warp's own, already read, columns
-          uint32_t hi2[8], lo2[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float a = __uint_as_float(sh[2 * i]), bb = __uint_as_float(sh[2 * i + 1]);
-            const __half2 hv = __floats2half2_rn(a, bb);
-            const float2 hf = __half22float2(hv);
-            const __half2 lv = __floats2half2_rn(a - hf.x, bb - hf.y);
-            hi2[i] = *reinterpret_cast<const uint32_t*>(&hv);
-            lo2[i] = *reinterpret_cast<const uint32_t*>(&lv);
-          }
-          const uint32_t kc = tbase + lane_off + Ly::T_S + b * 128 + h * 32 + half * 8;
-          tmem_st8(kc, hi2);
-          tmem_st8(kc + Ly::T_X, lo2);
-        } else {
-          tmem_st16(sa, sh);
-        }
-        if (SPLIT && !F16) {
+        tmem_st16(sa, sh);
+        if (SPLIT) {
           // K_lo as BF16 pairs (even column in the low half) into this warp's
           // own S_x columns, already read above: [32h + 8 half, +8)
           uint32_t lo2[8];
@@ -504,8 +549,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
                 __floats2bfloat162_rn(__uint_as_float(sx[2 * i]), __uint_as_float(sx[2 * i + 1]));
             lo2[i] = *reinterpret_cast<const uint32_t*>(&v);
           }
-          tmem_st8(tbase + lane_off + Ly::T_S + b * 128 + Ly::T_X + h * 32 + half * 8, lo2);
+          tmem_st8(tbase + lane_off + Ly::T_S + b * Ly::SBW + Ly::T_X + h * 32 + half * 8, lo2);
         }
+      }
       }
       tmem_wait_st();
       fence_before();

@@ -38,13 +38,26 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about `ns` nanoseconds pass, instead of spinning on issue
+// slots that the other warps of the SM need.
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: false on timeout or when another role already failed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* fail) {
   if (mbar_test(b, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t i = 1;; ++i) {
-    if (mbar_test(b, parity)) return true;
-    if ((i & 255) == 0) {
+    if (mbar_test_sleep(b, parity, 20000u)) return true;
+    if ((i & 15) == 0) {
       if (*reinterpret_cast<volatile int*>(fail)) return false;
       if (clock64() - t0 > kWaitCycles) {
         atomicExch(fail, 1);
