@@ -475,10 +475,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
             const int cc = half * 16 + c;
             const float4 n4 = snb[cc >> 2];
             const float nbc = (cc & 3) == 0 ? n4.x : (cc & 3) == 1 ? n4.y : (cc & 3) == 2 ? n4.z : n4.w;
-            const float u2 = fmaxf(fmaf(m2, __uint_as_float(s32[cc]), na + nbc), 1e-30f);
-            const float rs = rsqrt_approx(u2);
-            const float uu = u2 * rs;
-            kf[c] = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx(fmaf(-u2, rs, (float)kKExp));
+            const float u2 = fmaf(m2, __uint_as_float(s32[cc]), na + nbc);
+            const float uu = sqrt_abs_approx(u2);
+            kf[c] = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx((float)kKExp - uu);
           }
           if (diag) {
             const int64_t dc = grow - (col0 + h * 32 + half * 16);
