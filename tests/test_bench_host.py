@@ -1,0 +1,67 @@
+"""Host logic of the benchmark and the binding (no GPU): the roofline's
+per-entry work and the peak it divides by for each precision, the reported
+traffic, and the precision constants against the C header."""
+import os
+import re
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1700.0}
+
+
+def test_split_forms_count_three_products():
+    # d = 64, t = 16: 2 (d + t) = 160 per product
+    assert bench.tensor_flops_per_entry("split_f16", 64, 16) == 480.0
+    assert bench.tensor_flops_per_entry("split_tf32", 64, 16) == 480.0
+    assert bench.tensor_flops_per_entry("tf32", 64, 16) == 160.0
+
+
+def test_roofline_peak_follows_the_operand_type():
+    ent = 1.0e12
+    f16 = bench.roofline("split_f16", 64, 16, ent, 2070.0, PEAKS, "test")
+    tf32 = bench.roofline("split_tf32", 64, 16, ent, 2070.0, PEAKS, "test")
+    assert f16["bound"] == tf32["bound"] == "tensor"
+    assert f16["achieved"] == pytest.approx(480.0)          # 1e12 x 480 / 1e12
+    assert f16["peak"] == pytest.approx(2000.0)             # FP16 = BF16 dense rate
+    assert tf32["peak"] == pytest.approx(2000.0 * 1.1 / 2.25)
+    assert f16["frac"] == pytest.approx(480.0 / 2000.0)
+    assert tf32["frac"] == pytest.approx(2 * f16["frac"] * 2.25 / 2.2)
+
+
+def test_roofline_fp32_is_alu_bound():
+    r = bench.roofline("fp32", 64, 16, 1.0e11, 2000.0, PEAKS, "test")
+    assert r["bound"] == "alu"
+    assert r["peak"] == pytest.approx(152 * 128 * 2000.0e6 / 1e12)
+    assert r["achieved"] == pytest.approx(1.0e11 * (64 + 16 + 12) / 1e12)
+
+
+def test_stale_traffic_is_not_reported():
+    # counters taken on an earlier kernel are not carried over
+    assert bench.KMV_DRAM_BYTES.get(("gp1m", "split_f16")) is None
+
+
+def test_precision_constants_match_header():
+    src = open(os.path.join(ROOT, "include", "gp.h")).read()
+    enum = dict((m.group(1), int(m.group(2)))
+                for m in re.finditer(r"\b(GP_(?:FP32_PLAIN|FP32_SPLIT_TF32|FP32_SPLIT_F16|TF32))\s*=\s*(\d+)", src))
+    from paper_2109_09817_gb300 import _lib
+    assert enum == {"GP_FP32_PLAIN": _lib.GP_FP32_PLAIN, "GP_FP32_SPLIT_TF32": _lib.GP_FP32_SPLIT_TF32,
+                    "GP_FP32_SPLIT_F16": _lib.GP_FP32_SPLIT_F16, "GP_TF32": _lib.GP_TF32}
+    assert "GP_BF16" not in src
+
+
+def test_bench_default_is_split_f16():
+    sys_argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        args = bench.parse()
+    finally:
+        sys.argv = sys_argv
+    assert args.precision == "split_f16" and args.warmup >= 3 and args.gpus == 1
