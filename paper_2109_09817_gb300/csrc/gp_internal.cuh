@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -137,6 +138,19 @@ T* ws(gp_ctx* ctx, int slot, size_t count) {
   return static_cast<T*>(ws_get(ctx, slot, count * sizeof(T)));
 }
 void* pinned_get(gp_ctx* ctx, size_t bytes);
+
+// Raises a kernel's dynamic shared-memory limit once per device: the
+// attribute belongs to the device that is current, so a process driving
+// several devices (or several threads driving one) needs a per-device,
+// thread-safe record.  `done` is one static mask per kernel instance.
+template <class Kernel>
+int smem_attr_once(gp_ctx* ctx, Kernel* kernel, size_t smem, std::atomic<uint64_t>& done) {
+  const uint64_t bit = 1ull << (ctx->device & 63);
+  if (done.load(std::memory_order_acquire) & bit) return GP_OK;
+  GP_CUDA(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  done.fetch_or(bit, std::memory_order_release);
+  return GP_OK;
+}
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -230,12 +230,8 @@ int launch_grad(gp_ctx* ctx, const Prep& p, const float* U, const float* W,
   const size_t smem = sizeof(float) * (size_t)(BM * SX + BN * SX + BM * SP + BN * SP +
                                                BN * SKS + BM + BN + BM) +
                       sizeof(double) * (16 * DP + 32);
-  static bool attr = false;
-  if (!attr) {
-    GP_CUDA(ctx, cudaFuncSetAttribute(grad_kernel<DP, PW>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  GP_TRY(smem_attr_once(ctx, grad_kernel<DP, PW>, smem, attr));
   const int64_t row_tiles = ceil_div(p.n, BM), col_tiles = ceil_div(p.n, BN);
   int64_t splits = std::max<int64_t>(1, ceil_div(4LL * ctx->num_sms, row_tiles));
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, col_tiles / 4));

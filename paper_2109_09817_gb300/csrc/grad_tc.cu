@@ -452,12 +452,8 @@ int launch_grad_tc(gp_ctx* ctx, const Prep& pr, const float* U, const float* W, 
   int* status = device_status(ctx);
   if (!status) return set_err(ctx, GP_ENOMEM, "workspace (status)");
   const size_t smem = Ly::TOTAL + 1024;
-  static bool attr = false;
-  if (!attr) {
-    GP_CUDA(ctx, cudaFuncSetAttribute(grad_tc_kernel<DP, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  GP_TRY(smem_attr_once(ctx, grad_tc_kernel<DP, PW>, smem, attr));
   const int64_t row_tiles = ceil_div(pr.n, GBM), col_tiles = ceil_div(pr.n, GBN);
   int64_t splits = std::max<int64_t>(1, ceil_div(4LL * ctx->num_sms, row_tiles));
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, col_tiles / 4));

@@ -201,13 +201,8 @@ int launch_plain(gp_ctx* ctx, const Prep& rows, const Prep& cols,
                  float s, bool sym) {
   const size_t smem = sizeof(float) * (BM * SXS + BN * SXS + BN * SKS +
                                        TC * (BN + 1) + BM + BN);
-  static bool attr_set = false;
-  if (!attr_set) {
-    GP_CUDA(ctx, cudaFuncSetAttribute(kmv_plain_kernel<TC>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  GP_TRY(smem_attr_once(ctx, kmv_plain_kernel<TC>, smem, attr));
   const int64_t row_tiles = ceil_div(rows.n, BM);
   const int64_t col_tiles = ceil_div(cols.n, BN);
   // enough CTAs for ~4 waves at 2 CTAs per SM, at least 4 J tiles per CTA

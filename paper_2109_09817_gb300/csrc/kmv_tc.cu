@@ -666,12 +666,8 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const void* vhi, 
     }
   }
   const size_t smem = Ly::TOTAL + 1024;
-  static bool attr = false;
-  if (!attr) {
-    GP_CUDA(ctx, cudaFuncSetAttribute(kmv_tc_kernel<DP, T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  GP_TRY(smem_attr_once(ctx, kmv_tc_kernel<DP, T, OP>, smem, attr));
   const int64_t row_tiles = ceil_div(rows.n, BM);
   const int64_t col_tiles = ceil_div(cols.n, BN);
   int64_t splits = std::max<int64_t>(1, ceil_div(4LL * ctx->num_sms, row_tiles));
