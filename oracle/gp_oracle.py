@@ -49,6 +49,7 @@ __all__ = [
     "same_probe_logdet_target", "dkhat_dtheta", "exact_grad",
     "same_probe_grad", "predict", "true_relative_residual",
     "sym_precond_factor", "sym_precond_apply", "bcg",
+    "lanczos_variance_cache", "cached_variance",
 ]
 
 
@@ -488,3 +489,49 @@ def predict(X, y, Xp, lengthscale, s, sigma2, observation_noise=False):
     if observation_noise:
         var = var + sigma2
     return mean, var
+
+
+# ----------------------------------------------------------------------------
+# Variance cache for serving (the low-rank Lanczos cache of Pleiss et al.,
+# 2018, "LOVE"; a reading for the latent variance of Eq. (pred) at sizes
+# where one solve per test row is out of reach)
+# ----------------------------------------------------------------------------
+def lanczos_variance_cache(Khat, b, m):
+    """m steps of Lanczos on K-hat started at b, with full
+    reorthogonalisation in FP64: Q^T K-hat Q = T, Q orthonormal (N x m'),
+    m' <= m (fewer when b's Krylov space is exhausted).  K-hat^{-1} is
+    approximated by Q T^{-1} Q^T = R R^T with R = Q C^{-T}, T = C C^T.
+    Returns (R, T)."""
+    Khat = np.asarray(Khat, F64)
+    b = np.asarray(b, F64)
+    N = Khat.shape[0]
+    Q = np.zeros((N, m))
+    alpha = np.zeros(m)
+    beta = np.zeros(m)
+    q = b / np.linalg.norm(b)
+    q_prev = np.zeros(N)
+    steps = 0
+    for j in range(m):
+        Q[:, j] = q
+        w = Khat @ q - (beta[j - 1] * q_prev if j > 0 else 0.0)
+        alpha[j] = q @ w
+        w = w - alpha[j] * q
+        for _ in range(2):                      # full reorthogonalisation
+            w = w - Q[:, :j + 1] @ (Q[:, :j + 1].T @ w)
+        steps = j + 1
+        beta[j] = np.linalg.norm(w)
+        if beta[j] <= 1e-12 * abs(alpha[0]):
+            break
+        q_prev, q = q, w / beta[j]
+    Q = Q[:, :steps]
+    T = np.diag(alpha[:steps]) + np.diag(beta[:steps - 1], 1) + np.diag(beta[:steps - 1], -1)
+    C = np.linalg.cholesky(T)
+    R = sla.solve_triangular(C, Q.T, lower=True).T      # Q C^{-T}
+    return R, T
+
+
+def cached_variance(X, Xp, lengthscale, s, R):
+    """var_i ~ k(x'_i, x'_i) - |R^T k_i|^2 with k_i = K(X, x'_i)."""
+    Ks = kernel_matrix(Xp, X, lengthscale, s)
+    return s - np.sum((Ks @ R) ** 2, axis=1)
+
