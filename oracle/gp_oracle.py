@@ -26,6 +26,9 @@ Readings where the paper is silent (all listed in the design notes):
   P = L L^T + D, D = diag(K - L L^T) + sigma^2 I (the residual diagonal of
   the same factorisation), which equals the first form when K is close to
   rank k and stays well conditioned when K is close to diagonal.
+* Serving variances at sizes where one solve per test row is out of reach
+  use a low-rank Lanczos cache of K-hat^{-1} (Pleiss et al., 2018); the
+  paper does not say how it serves variances.
 """
 from __future__ import annotations
 
