@@ -210,7 +210,7 @@ GP_API int gp_bcg(gp_ctx* ctx, const float* X, int64_t N, int d,
  * Omega = 0: solve K-hat delta = R with preconditioned mBCG whose products use
  * `inner_precision` (e.g. GP_TF32), to relative residual `inner_tol`; then
  * Omega += delta and R = B - K-hat Omega with products in `outer_precision`
- * (GP_FP32_SPLIT_TF32 or GP_FP32_PLAIN).  A column stops once
+ * (GP_FP32_SPLIT_TF32, GP_FP32_SPLIT_F16 or GP_FP32_PLAIN).  A column stops once
  * ||R_c|| / ||B_c|| < tol (its R is zeroed, so later inner solves skip it);
  * the loop ends when every column has stopped or after max_outer rounds.
  * Preconditioner as in gp_mbcg (L, k, resid_diag).  B, Omega: device, N x t
@@ -242,7 +242,9 @@ GP_API int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
  * logml, logdet, logdet_stderr (standard error over probes, nullable),
  * grad (d + 2 doubles: dL/dl_1..dL/dl_d, dL/ds, dL/dsigma^2; nullable to
  * skip the gradient pass), stats (nullable).  1 <= n_probes <= 255.
- * Synchronises. */
+ * `precision` is the arithmetic of the K-hat products; with either split
+ * form the gradient pass runs on the tensor cores in split TF32 (the split
+ * FP16 form prepares the TF32 split features as well).  Synchronises. */
 GP_API int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
                       const gp_theta* theta, const float* y, int n_probes,
                       uint64_t seed, int k, int precond, double tol, int max_iter,
