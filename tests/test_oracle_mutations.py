@@ -7,10 +7,10 @@ rather than restating it.
 """
 import numpy as np
 import pytest
-import scipy.linalg as sla
 
 from oracle import gp_oracle as go
 
+import test_oracle_bcg as pins_bcg
 import test_oracle_grad_predict as pins_grad
 import test_oracle_kernel as pins_kernel
 import test_oracle_love as pins_love
@@ -67,6 +67,32 @@ def _mutants():
     def trr_no_noise(X, ell, s, sig2, Omega, B, rows=None):
         return orig_trr(X, ell, s, 0.0, Omega, B, rows)
 
+    orig_sym = go.sym_precond_factor
+    orig_pred = go.predict
+
+    def sym_wrong_root(L, sig2, resid=None):
+        # (1 + lam)^{-1} - 1 in place of (1 + lam)^{-1/2} - 1: the factor of
+        # P^{-1} itself instead of its square root
+        dh, Lt, Cp = orig_sym(L, sig2, resid)
+        lam, V = np.linalg.eigh(Lt.T @ Lt)
+        lam = np.maximum(lam, 0.0)
+        return dh, Lt, (V * (-1.0 / (1.0 + lam))) @ V.T
+
+    def signs_low_bit(seed, counters):
+        # the sign taken from the lowest output bit instead of the highest
+        with np.errstate(over="ignore"):
+            c = np.asarray(counters, dtype=np.uint64)
+            z = np.uint64(seed) + (c + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+            z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            z = z ^ (z >> np.uint64(31))
+        return np.where((z & np.uint64(1)) == 0, 1.0, -1.0)
+
+    def predict_no_prior(X, y, Xp, ell, s, sig2, observation_noise=False):
+        # Eq. (pred) read literally, without the prior term k(x', x')
+        mean, var = orig_pred(X, y, Xp, ell, s, sig2, observation_noise)
+        return mean, var - s
+
     return [
         ("matern52_of_r2", _matern_wrong_quadratic, pins_kernel.test_matern52_equals_bessel_family),
         ("khat_matmul", khat_no_noise, pins_kernel.test_khat_products_vs_brute_force),
@@ -76,6 +102,9 @@ def _mutants():
         ("pivoted_cholesky", piv_reversed, pins_solve.test_pivchol_matches_lapack_dpstrf),
         ("exact_grad", _grad_full_trace, pins_grad.test_exact_grad_vs_logspace_central_fd),
         ("lanczos_variance_cache", cache_untransposed, pins_love.test_full_basis_gives_exact_variance),
+        ("sym_precond_factor", sym_wrong_root, pins_bcg.test_sym_factor_is_inverse_square_root),
+        ("splitmix64_signs", signs_low_bit, pins_solve.test_splitmix64_published_outputs),
+        ("predict", predict_no_prior, pins_grad.test_predict_interpolates_and_bounds),
     ]
 
 
