@@ -455,8 +455,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
       fence_after();
       const bool diag = p.sym && row0 < col0 + BN && col0 < row0 + BM;
       if constexpr (F16) {
-        // All 32 of this warp's S columns at once.  K is held as 2^14 K (the
-        // scale rides in the exponent, 2^(14 - u)) and split into FP16
+        // All 32 of this warp's S columns at once.  u^2 = n_a + n_b + m2 S and
+        // u = sqrt(|u^2|) in one MUFU op (the modulus absorbs a u^2 rounded
+        // below zero).  K is held as 2^14 K (the scale rides in the
+        // exponent, 2^(14 - u)) and split into FP16
         // hi = fp16(K) and lo = fp16(K - hi), K - hi being exact in FP32, so
         // hi + lo = K to 2^-22.  They are packed two per 32-bit column (even
         // column in the low half): K_hi of columns [32h + 16 half, +16) to
