@@ -84,8 +84,32 @@ enum {
                        when K is close to diagonal)                          */
 };
 
-/* posterior variance modes of gp_predict */
-enum { GP_VAR_NONE = 0, GP_VAR_EXACT = 1 };
+/* stop rules of the CG solves (gp_mbcg, gp_logml_and_grad, gp_model_fit) */
+enum {
+  GP_STOP_RECURRENCE = 0, /* a column stops when its CG recurrence residual
+                             ||r_c|| / ||b_c|| is below tol (Sec. 4)        */
+  GP_STOP_TRUE = 1        /* as GP_STOP_RECURRENCE, then the solution
+                             columns are verified: one K-hat product of the
+                             iterate measures ||b_c - K-hat w_c|| / ||b_c||,
+                             and a column not below 0.8 tol continues its own
+                             recurrence to a proportionally lower target (its
+                             CG coefficients stay one unbroken Lanczos
+                             sequence); at most 4 verifications, after which
+                             a column still above 0.8 tol gives GP_ENOTCONV.
+                             In FP32 storage the attainable true residual is
+                             bounded below by rounding (about 1e-6 to 1e-5 on
+                             ill-conditioned K-hat), so tight tolerances need
+                             GP_STOP_RECURRENCE.                             */
+};
+
+/* posterior variance modes of gp_predict / gp_predict_sum */
+enum {
+  GP_VAR_NONE = 0,
+  GP_VAR_EXACT = 1,   /* K-hat^{-1} by preconditioned CG solves              */
+  GP_VAR_CACHED = 2   /* K-hat^{-1} ~ R R^T from the model's Lanczos cache
+                         (gp_model_variance_cache)                          */
+};
+#define GP_VAR_CACHE_MAX_RANK 128
 
 typedef struct gp_ctx gp_ctx;
 typedef struct gp_model gp_model;
@@ -108,6 +132,9 @@ typedef struct {
   double relres_max;    /* max over columns                                  */
   double logdet_P;      /* log|P|, P = L L^T + sigma^2 I                    */
   double yKinvy;        /* y^T K-hat^{-1} y                                  */
+  double true_relres_y; /* ||y - K-hat a|| / ||y|| measured by one product of
+                           the final iterate (-1 if not measured)           */
+  int true_checks;      /* products spent on those measurements             */
 } gp_stats;
 
 /* ---- context -------------------------------------------------------------
@@ -122,12 +149,21 @@ GP_API int gp_sync(gp_ctx* ctx);
 GP_API const char* gp_last_error(const gp_ctx* ctx);
 /* Number of kernels this context has launched (diagnostics). */
 GP_API int64_t gp_launch_count(const gp_ctx* ctx);
+/* Context options.  GP_OPT_SYMMETRIC_KMV (default 1): K-hat V products in
+ * GP_FP32_SPLIT_F16 use K's symmetry, forming only the tiles at and right of
+ * the diagonal blocks and contracting each twice (K_IJ V_J and K_IJ^T V_I);
+ * 0 selects the full-grid kernel (every tile formed once), for comparisons.
+ * GP_EINVAL for an unknown option or value. */
+enum { GP_OPT_SYMMETRIC_KMV = 1 };
+GP_API int gp_set_option(gp_ctx* ctx, int option, int value);
 /* K-hat V timing: gp_profile(ctx, 1) resets the counters and records a CUDA
  * event pair on the context's stream around every K-hat V product issued
  * from then on (gp_profile(ctx, 0) stops recording).  gp_profile_read
  * synchronises and returns (HOST outputs) the number of products, their
  * summed device time in ms, their GEMM-equivalent flops 2 m n (d + t) and
- * their kernel entries m n (m, n = rows and columns of the K tile grid). */
+ * the kernel entries they evaluated: m n (m, n = rows and columns of the
+ * product), or, for the symmetric split-FP16 product, the entries of the
+ * tiles at and right of the diagonal blocks (about n^2 / 2). */
 GP_API int gp_profile(gp_ctx* ctx, int enable);
 GP_API int gp_profile_read(gp_ctx* ctx, int64_t* products, double* ms,
                            double* flops, double* entries);
@@ -175,12 +211,16 @@ GP_API int gp_pivchol(gp_ctx* ctx, const float* X, int64_t N, int d,
  * B, Omega: t vectors of length N (column-major).  alpha_hist, beta_hist:
  * nullable device FP64 arrays of max_iter*t, entry [j*t + c] = the CG
  * coefficient of column c at step j (0 after the column stopped); the
- * Lanczos tridiagonal of column c follows from its first iters[c] entries.
- * iters, rel_resid: nullable HOST arrays of t.  Synchronises. */
+ * Lanczos tridiagonal of column c follows from its first iters[c] entries
+ * (entries are indexed by the column's own steps).  stop_rule: GP_STOP_
+ * RECURRENCE, or GP_STOP_TRUE to verify every column's true residual (one
+ * extra product per verification).  iters, rel_resid: nullable HOST arrays
+ * of t; rel_resid holds the measured true residuals under GP_STOP_TRUE, the
+ * recurrence residuals otherwise.  Synchronises. */
 GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
             const gp_theta* theta, const double* L, int k,
             const double* resid_diag, const float* B,
-            int t, double tol, int max_iter, int precision, float* Omega,
+            int t, double tol, int max_iter, int stop_rule, int precision, float* Omega,
             double* alpha_hist, double* beta_hist, int* iters,
             double* rel_resid);
 
@@ -211,7 +251,8 @@ GP_API int gp_bcg(gp_ctx* ctx, const float* X, int64_t N, int d,
  * `inner_precision` (e.g. GP_TF32), to relative residual `inner_tol`; then
  * Omega += delta and R = B - K-hat Omega with products in `outer_precision`
  * (GP_FP32_SPLIT_TF32, GP_FP32_SPLIT_F16 or GP_FP32_PLAIN).  A column stops once
- * ||R_c|| / ||B_c|| < tol (its R is zeroed, so later inner solves skip it);
+ * ||R_c|| / ||B_c|| < 0.8 tol (the margin of GP_STOP_TRUE for the measuring
+ * product's own error; its R is zeroed, so later inner solves skip it);
  * the loop ends when every column has stopped or after max_outer rounds.
  * Preconditioner as in gp_mbcg (L, k, resid_diag).  B, Omega: device, N x t
  * column-major (ld N).  outer_steps, inner_steps (total inner CG steps over
@@ -244,11 +285,14 @@ GP_API int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
  * skip the gradient pass), stats (nullable).  1 <= n_probes <= 255.
  * `precision` is the arithmetic of the K-hat products; with either split
  * form the gradient pass runs on the tensor cores in split TF32 (the split
- * FP16 form prepares the TF32 split features as well).  Synchronises. */
+ * FP16 form prepares the TF32 split features as well).  stop_rule
+ * (GP_STOP_RECURRENCE or GP_STOP_TRUE) applies to y's column, the solve
+ * a = K-hat^{-1} y; the probe columns stop by their recurrences.
+ * Synchronises. */
 GP_API int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
                       const gp_theta* theta, const float* y, int n_probes,
                       uint64_t seed, int k, int precond, double tol, int max_iter,
-                      int precision, double* logml, double* logdet,
+                      int stop_rule, int precision, double* logml, double* logdet,
                       double* grad, double* logdet_stderr, gp_stats* stats);
 
 /* ---- K-hat V without any allocation ---------------------------------------
@@ -289,27 +333,63 @@ GP_API int gp_kmatmul_noalloc(const float* X, int64_t N, int d,
  * the symmetric Nystrom preconditioner (as gp_bcg), stopping when y's
  * residual is below tol; a = column 0 (the block Krylov space contains y's
  * own, so y converges in fewer steps; a product costs the same for up to 16
- * vectors).  X and y are copied; the caller may free them afterwards.
+ * vectors).  stop_rule (block = 1 only; block CG stops by its recurrence):
+ * GP_STOP_RECURRENCE or GP_STOP_TRUE for the solve of y.  X and y are copied; the caller may free them afterwards.
  * GP_ENOTCONV / GP_EBREAKDOWN: no model is returned.  Synchronises. */
 GP_API int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
                  const gp_theta* theta, const float* y, int k, int precond, int block,
-                 double tol, int max_iter, int precision, gp_model** out,
+                 double tol, int max_iter, int stop_rule, int precision, gp_model** out,
                  gp_stats* stats);
 GP_API void gp_model_free(gp_model* model);
 
 /* mean = K(X', X) a.  var (nullable): var_mode GP_VAR_EXACT gives the latent
  * posterior variance k(x', x') - k*^T K-hat^{-1} k* (Eq. pred read as the
  * standard posterior variance) by an mBCG solve with the M columns k* as
- * right-hand sides (to the model's tol).  Xp: M x d row-major; mean, var: M
- * floats.  Synchronises when var is requested. */
+ * right-hand sides (to the model's tol); GP_VAR_CACHED reads it from the
+ * model's variance cache (GP_EINVAL without one) with one cross product.
+ * Xp: M x d row-major; mean, var: M floats.  Synchronises when var is
+ * requested with GP_VAR_EXACT. */
 GP_API int gp_predict(gp_ctx* ctx, const gp_model* model, const float* Xp, int64_t M,
                float* mean, float* var, int var_mode);
+
+/* ---- variance cache (Eq. pred at sizes where one solve per test row is
+ * out of reach) --------------------------------------------------------------
+ * The paper does not say how it serves variances; this is the low-rank
+ * Lanczos cache of Pleiss et al. (2018).  `rank` (1 <= rank <=
+ * GP_VAR_CACHE_MAX_RANK) steps of Lanczos on K-hat from the start vector b
+ * (device, N floats; NULL = K-hat a, which is y up to the fit's tolerance),
+ * with full reorthogonalisation (FP32 vectors, FP64 coefficients and dot
+ * products), give K-hat Q ~ Q T; the model keeps R = Q C^{-T}, T = C C^T,
+ * so that K-hat^{-1} ~ R R^T and the latent variance is read as
+ * k(x',x') - |R^T k*|^2 (an upper bound of the exact variance that tightens
+ * as the rank grows; exact with a full Krylov basis).  Costs `rank` K-hat
+ * products; the cache takes rank x N floats of device memory, owned by the
+ * model (freed by gp_model_free).  *rank_out: the steps taken (fewer when
+ * b's Krylov space is exhausted).  GP_EBREAKDOWN if T is not positive
+ * definite.  Synchronises. */
+GP_API int gp_model_variance_cache(gp_ctx* ctx, gp_model* model, const float* b, int rank,
+                                   int* rank_out);
+
+/* Per-molecule prediction (Sec. 2.1: a molecule's correlation energy is the
+ * sum of its pair energies): over the M rows of Xp (device, M x d), the
+ * HOST outputs mean_sum = sum_i E[f(x'_i)] and var_sum (nullable) =
+ * Var[sum_i f(x'_i)] = 1^T K(X',X') 1 - c^T K-hat^{-1} c with c = K(X,X') 1,
+ * every cross-covariance between the molecule's rows included.  var_mode
+ * GP_VAR_EXACT solves for K-hat^{-1} c (one CG solve to the model's tol);
+ * GP_VAR_CACHED uses the model's cache (|R^T c|^2).  1^T K(X',X') 1 is summed
+ * in FP64 from kernel entries formed by direct differences.  A diagonal and
+ * an off-diagonal model are independent GPs: their sums and variances add.
+ * Synchronises. */
+GP_API int gp_predict_sum(gp_ctx* ctx, const gp_model* model, const float* Xp, int64_t M,
+                          double* mean_sum, double* var_sum, int var_mode);
 
 /* ---- serving: continuous batching over resident models (Eq. pred) --------
  * A gp_server holds trained models on one device and serves two request
  * kinds from host memory:
- *  - predict: the mean K(X', X) a of one request's M feature rows against a
- *    resident model.  Each model has its own stream and batching thread:
+ *  - predict: the mean K(X', X) a (and, from the model's variance cache, the
+ *    latent variances) of one request's M feature rows against a resident
+ *    model; a molecule request sums the predictions of its diagonal and
+ *    off-diagonal pair rows over two models, with the variance of the sum.  Each model has its own stream and batching thread:
  *    every request queued when a batch starts (up to max_batch_rows rows) is
  *    packed into ONE fused K(X', X) a launch; requests arriving meanwhile join
  *    the next batch.  Batches of different models overlap on the device.
@@ -330,17 +410,33 @@ typedef struct gp_server gp_server;
 GP_API int gp_server_create(gp_server** out, int device, int64_t max_batch_rows,
                             double reserve_bytes);
 /* Fit a model from DEVICE arrays X (N x d) and y (N) as gp_model_fit does
- * (block = 1),
+ * (block = 1, GP_STOP_RECURRENCE), build its variance cache of rank var_rank
+ * (0 = none; 1 <= var_rank <= GP_VAR_CACHE_MAX_RANK, started at K-hat a),
  * keep it resident and start its batching thread; *model_id is its index.
- * Synchronises; errors as gp_model_fit (message in gp_server_last_error). */
+ * Synchronises; errors as gp_model_fit and gp_model_variance_cache (message
+ * in gp_server_last_error). */
 GP_API int gp_server_add_model(gp_server* srv, const float* X, int64_t N, int d,
                                const gp_theta* theta, const float* y, int k, int precond,
-                               double tol, int max_iter, int precision, int* model_id);
-/* Queue a predict request: Xp HOST M x d row-major, mean HOST M floats
- * (written before the request completes).  GP_EINVAL for an unknown model,
- * M < 1 or M > max_batch_rows. */
+                               double tol, int max_iter, int precision, int var_rank,
+                               int* model_id);
+/* Queue a predict request: Xp HOST M x d row-major, mean HOST M floats, var
+ * HOST M floats or NULL (the latent variances from the model's variance
+ * cache), both written before the request completes.  GP_EINVAL for an
+ * unknown model, M < 1, M > max_batch_rows, or var without a cache. */
 GP_API int gp_server_predict(gp_server* srv, int model_id, const float* Xp, int64_t M,
-                             float* mean, uint64_t* ticket);
+                             float* mean, float* var, uint64_t* ticket);
+/* Queue a molecule request (Sec. 2.1: the correlation energy is the sum of
+ * the pair energies): Xd HOST Md x d, the molecule's diagonal pair rows for
+ * model diag_model; Xo HOST Mo x d (Mo >= 0), its off-diagonal pair rows for
+ * model off_model.  energy HOST 2 doubles, written before completion:
+ * [0] = the sum of the predictive means over all Md + Mo rows, [1] = the
+ * variance of that sum (cross-covariances within each model's rows from the
+ * models' variance caches; the two models are independent GPs).  Both parts
+ * join their models' batches.  GP_EINVAL for unknown models, sizes out of
+ * range, or a model without a variance cache. */
+GP_API int gp_server_molecule(gp_server* srv, int diag_model, const float* Xd, int64_t Md,
+                              int off_model, const float* Xo, int64_t Mo, double* energy,
+                              uint64_t* ticket);
 /* Queue a solve request: X HOST N x d, y HOST N, alpha HOST N (out). */
 GP_API int gp_server_solve(gp_server* srv, const float* X, int64_t N, int d,
                            const gp_theta* theta, const float* y, int k, double tol,

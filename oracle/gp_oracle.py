@@ -29,6 +29,11 @@ Readings where the paper is silent (all listed in the design notes):
 * Serving variances at sizes where one solve per test row is out of reach
   use a low-rank Lanczos cache of K-hat^{-1} (Pleiss et al., 2018); the
   paper does not say how it serves variances.
+* A molecule's correlation energy is the sum of its pair energies (Sec. 2.1,
+  MOB-ML); its predictive variance is read as the variance of the sum of
+  the latent values at the molecule's feature rows, 1^T Cov 1 with Cov the
+  posterior covariance of Eq. (pred) (cross-covariances included), and the
+  diagonal and off-diagonal models as independent GPs whose variances add.
 """
 from __future__ import annotations
 
@@ -52,7 +57,7 @@ __all__ = [
     "same_probe_logdet_target", "dkhat_dtheta", "exact_grad",
     "same_probe_grad", "predict", "true_relative_residual",
     "sym_precond_factor", "sym_precond_apply", "bcg",
-    "lanczos_variance_cache", "cached_variance",
+    "lanczos_variance_cache", "cached_variance", "predict_sum", "cached_variance_sum",
 ]
 
 
@@ -538,3 +543,33 @@ def cached_variance(X, Xp, lengthscale, s, R):
     Ks = kernel_matrix(Xp, X, lengthscale, s)
     return s - np.sum((Ks @ R) ** 2, axis=1)
 
+
+# ----------------------------------------------------------------------------
+# Per-molecule sums (Sec. 2.1: E_corr is the sum of a molecule's pair
+# energies; Eq. (pred) for each pair's latent value)
+# ----------------------------------------------------------------------------
+def predict_sum(X, y, Xp, lengthscale, s, sigma2):
+    """Mean and variance of S = sum_i f(x'_i) over the M rows of X' under the
+    posterior of Eq. (pred): E[S] = 1^T K(X',X) K-hat^{-1} y and
+    Var[S] = 1^T K(X',X') 1 - c^T K-hat^{-1} c with c = K(X,X') 1, i.e. the
+    sum of every entry of the posterior covariance (variances and the
+    cross-covariances between the molecule's rows)."""
+    Khat = khat_matrix(X, lengthscale, s, sigma2)
+    Ks = kernel_matrix(Xp, X, lengthscale, s)
+    Kss = kernel_matrix(Xp, Xp, lengthscale, s)
+    ch = sla.cho_factor(Khat, lower=True)
+    ones = np.ones(len(Xp))
+    mean = ones @ (Ks @ sla.cho_solve(ch, np.asarray(y, F64)))
+    c = Ks.T @ ones
+    var = ones @ Kss @ ones - c @ sla.cho_solve(ch, c)
+    return float(mean), float(var)
+
+
+def cached_variance_sum(X, Xp, lengthscale, s, R):
+    """Var[S] with the Lanczos cache K-hat^{-1} ~ R R^T:
+    1^T K(X',X') 1 - |R^T K(X,X') 1|^2."""
+    Ks = kernel_matrix(Xp, X, lengthscale, s)
+    Kss = kernel_matrix(Xp, Xp, lengthscale, s)
+    ones = np.ones(len(Xp))
+    u = R.T @ (Ks.T @ ones)
+    return float(ones @ Kss @ ones - u @ u)

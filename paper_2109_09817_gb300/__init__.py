@@ -9,8 +9,8 @@ binding.  Importing it does not load the library; the first Context does,
 and fails loudly if libgp.so has not been built.
 """
 from ._lib import (GP_FP32_SPLIT_F16, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
-                   GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_PC_SIGMA, GP_PC_RESID, EXPORTS,
-                   LIB_PATH)
+                   GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_PC_SIGMA, GP_PC_RESID,
+                   GP_STOP_RECURRENCE, GP_STOP_TRUE, EXPORTS, LIB_PATH)
 
 
 def __getattr__(name):

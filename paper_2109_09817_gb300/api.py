@@ -18,8 +18,9 @@ import torch
 
 from . import _lib
 from ._lib import (GP_FP32_SPLIT_F16, GP_FP32_PLAIN, GP_FP32_SPLIT_TF32,  # noqa: F401
-                   GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_OK, GP_ENOTCONV,
-                   GP_EBREAKDOWN, GP_EINVAL, GP_PC_SIGMA, GP_PC_RESID, ERROR_NAMES)
+                   GP_TF32, GP_VAR_EXACT, GP_VAR_NONE, GP_VAR_CACHED, GP_OK, GP_ENOTCONV,
+                   GP_EBREAKDOWN, GP_EINVAL, GP_PC_SIGMA, GP_PC_RESID, ERROR_NAMES,
+                   GP_STOP_RECURRENCE, GP_STOP_TRUE)
 
 PRECISIONS = {"fp32": GP_FP32_PLAIN, "split_tf32": GP_FP32_SPLIT_TF32,
               "split_f16": GP_FP32_SPLIT_F16, "tf32": GP_TF32}
@@ -86,6 +87,10 @@ class Context:
 
     def sync(self):
         self.check(self.lib.gp_sync(self.h))
+
+    def set_option(self, option: int, value: int):
+        """gp_set_option (e.g. _lib.GP_OPT_SYMMETRIC_KMV, 0 or 1)."""
+        self.check(self.lib.gp_set_option(self.h, option, value))
 
 
 def _p(t: Optional[torch.Tensor]):
@@ -159,10 +164,12 @@ def gp_pivchol(ctx: Context, X: torch.Tensor, theta: Theta, k: int, want_resid: 
 def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tensor],
             B: torch.Tensor, tol: float = 1e-6, max_iter: int = 1000,
             precision: int = GP_FP32_PLAIN, allow_notconv: bool = True,
-            resid: Optional[torch.Tensor] = None):
+            resid: Optional[torch.Tensor] = None, stop: int = GP_STOP_RECURRENCE):
     """Batched PCG on K-hat Omega = B; returns dict(Omega, alpha, beta, iters,
     relres, rc).  L: (k, N) float64 from gp_pivchol or None; resid: its
-    residual diagonal for the GP_PC_RESID form, or None for P = L L^T + sigma^2 I."""
+    residual diagonal for the GP_PC_RESID form, or None for P = L L^T + sigma^2 I.
+    stop: GP_STOP_RECURRENCE or GP_STOP_TRUE (relres then holds the measured
+    true residuals)."""
     _dev(ctx, X, torch.float32, "X")
     N, d = X.shape
     B = _block(ctx, B, N, "B")
@@ -180,7 +187,7 @@ def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tenso
     if resid is not None:
         _dev(ctx, resid, torch.float64, "resid")
     rc = ctx.check(ctx.lib.gp_mbcg(ctx.h, _p(X), N, d, ctypes.byref(th), _p(L), k, _p(resid), _p(B), t,
-                                   tol, max_iter, precision, _p(Om), _p(ah), _p(bh), iters, rr),
+                                   tol, max_iter, stop, precision, _p(Om), _p(ah), _p(bh), iters, rr),
                    allow=allow)
     return dict(Omega=Om, alpha=ah, beta=bh, iters=np.array(iters[:]),
                 relres=np.array(rr[:]), rc=rc)
@@ -245,8 +252,9 @@ def gp_logml_and_grad(ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tens
                       n_probes: int = 15, seed: int = 0, k: int = 32, tol: float = 1e-6,
                       max_iter: int = 1000, precision: int = GP_FP32_PLAIN,
                       want_grad: bool = True, allow_notconv: bool = False,
-                      precond: int = GP_PC_SIGMA):
-    """Eq. (ll) and its gradient (natural parameters l_1..l_d, s, sigma^2)."""
+                      precond: int = GP_PC_SIGMA, stop: int = GP_STOP_RECURRENCE):
+    """Eq. (ll) and its gradient (natural parameters l_1..l_d, s, sigma^2).
+    stop applies to y's column (GP_STOP_TRUE: its true residual is verified)."""
     _dev(ctx, X, torch.float32, "X")
     _dev(ctx, y, torch.float32, "y")
     N, d = X.shape
@@ -259,7 +267,7 @@ def gp_logml_and_grad(ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tens
     allow = (GP_ENOTCONV,) if allow_notconv else ()
     rc = ctx.check(ctx.lib.gp_logml_and_grad(
         ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), n_probes, ctypes.c_uint64(seed), k, precond, tol,
-        max_iter, precision, ctypes.byref(logml), ctypes.byref(logdet),
+        max_iter, stop, precision, ctypes.byref(logml), ctypes.byref(logdet),
         grad if want_grad else None, ctypes.byref(se), ctypes.byref(stats)), allow=allow)
     return dict(logml=logml.value, logdet=logdet.value, logdet_stderr=se.value,
                 grad=np.array(grad[:]) if want_grad else None, stats=stats.as_dict(), rc=rc)
@@ -270,7 +278,8 @@ class Model:
 
     def __init__(self, ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tensor,
                  k: int = 32, tol: float = 1e-6, max_iter: int = 1000,
-                 precision: int = GP_FP32_PLAIN, precond: int = GP_PC_SIGMA, block: int = 1):
+                 precision: int = GP_FP32_PLAIN, precond: int = GP_PC_SIGMA, block: int = 1,
+                 stop: int = GP_STOP_RECURRENCE):
         _dev(ctx, X, torch.float32, "X")
         _dev(ctx, y, torch.float32, "y")
         self.ctx = ctx
@@ -280,7 +289,7 @@ class Model:
         stats = _lib.GpStats()
         th, keep = theta.as_c()
         ctx.check(ctx.lib.gp_model_fit(ctx.h, _p(X), N, d, ctypes.byref(th), _p(y), k, precond, block, tol,
-                                       max_iter, precision, ctypes.byref(h), ctypes.byref(stats)))
+                                       max_iter, stop, precision, ctypes.byref(h), ctypes.byref(stats)))
         self.h = h
         self.stats = stats.as_dict()
 
@@ -297,18 +306,42 @@ class Model:
 
 
 def gp_model_fit(ctx: Context, X, theta, y, k=32, tol=1e-6, max_iter=1000,
-                 precision=GP_FP32_PLAIN, precond=GP_PC_SIGMA, block=1) -> Model:
-    return Model(ctx, X, theta, y, k, tol, max_iter, precision, precond, block)
+                 precision=GP_FP32_PLAIN, precond=GP_PC_SIGMA, block=1,
+                 stop=GP_STOP_RECURRENCE) -> Model:
+    return Model(ctx, X, theta, y, k, tol, max_iter, precision, precond, block, stop)
 
 
 def gp_predict(ctx: Context, model: Model, Xp: torch.Tensor, var_mode: int = GP_VAR_NONE):
-    """Predictive mean (and latent variance with GP_VAR_EXACT), Eq. (pred)."""
+    """Predictive mean (and latent variance with GP_VAR_EXACT or
+    GP_VAR_CACHED), Eq. (pred)."""
     _dev(ctx, Xp, torch.float32, "Xp")
     M = Xp.shape[0]
     mean = torch.empty(M, dtype=torch.float32, device=Xp.device)
     var = torch.empty(M, dtype=torch.float32, device=Xp.device) if var_mode else None
     ctx.check(ctx.lib.gp_predict(ctx.h, model.h, _p(Xp), M, _p(mean), _p(var), var_mode))
     return mean, var
+
+
+def gp_model_variance_cache(ctx: Context, model: Model, rank: int,
+                            b: Optional[torch.Tensor] = None) -> int:
+    """Build the model's rank-`rank` Lanczos variance cache from the start
+    vector b (device, N floats; None = K-hat a); returns the steps taken."""
+    if b is not None:
+        _dev(ctx, b, torch.float32, "b")
+    out = ctypes.c_int(0)
+    ctx.check(ctx.lib.gp_model_variance_cache(ctx.h, model.h, _p(b), rank, ctypes.byref(out)))
+    return out.value
+
+
+def gp_predict_sum(ctx: Context, model: Model, Xp: torch.Tensor, var_mode: int = GP_VAR_NONE):
+    """(sum of the predictive means over the rows of Xp, variance of that sum
+    or None), Sec. 2.1's per-molecule energy."""
+    _dev(ctx, Xp, torch.float32, "Xp")
+    ms = ctypes.c_double()
+    vs = ctypes.c_double()
+    ctx.check(ctx.lib.gp_predict_sum(ctx.h, model.h, _p(Xp), Xp.shape[0], ctypes.byref(ms),
+                                     ctypes.byref(vs) if var_mode else None, var_mode))
+    return ms.value, (vs.value if var_mode else None)
 
 
 class Server:
@@ -335,25 +368,42 @@ class Server:
 
     def add_model(self, X: torch.Tensor, theta: Theta, y: torch.Tensor, k: int = 32,
                   precond: int = GP_PC_RESID, tol: float = 1e-4, max_iter: int = 1000,
-                  precision: int = GP_FP32_SPLIT_TF32) -> int:
+                  precision: int = GP_FP32_SPLIT_TF32, var_rank: int = 0) -> int:
         if not (X.is_cuda and y.is_cuda):
             raise ValueError("add_model takes device tensors")
         N, d = X.shape
         mid = ctypes.c_int(-1)
         th, keep = theta.as_c()
         self.check(self.lib.gp_server_add_model(self.h, _p(X), N, d, ctypes.byref(th), _p(y), k,
-                                                precond, tol, max_iter, precision,
+                                                precond, tol, max_iter, precision, var_rank,
                                                 ctypes.byref(mid)))
         return mid.value
 
-    def predict(self, model_id: int, Xp: np.ndarray):
+    def predict(self, model_id: int, Xp: np.ndarray, want_var: bool = False):
+        """Queue a predict request; wait() returns the means, or (means,
+        variances) with want_var."""
         Xp = np.ascontiguousarray(Xp, dtype=np.float32)
         mean = np.empty(Xp.shape[0], dtype=np.float32)
+        var = np.empty(Xp.shape[0], dtype=np.float32) if want_var else None
         tk = ctypes.c_uint64()
         self.check(self.lib.gp_server_predict(self.h, model_id, Xp.ctypes.data_as(ctypes.c_void_p),
                                               Xp.shape[0], mean.ctypes.data_as(ctypes.c_void_p),
+                                              var.ctypes.data_as(ctypes.c_void_p) if want_var else None,
                                               ctypes.byref(tk)))
-        self._keep[tk.value] = (Xp, mean)
+        self._keep[tk.value] = (Xp, (mean, var) if want_var else mean)
+        return tk.value
+
+    def molecule(self, diag_id: int, Xd: np.ndarray, off_id: int, Xo: np.ndarray):
+        """Queue a molecule request; wait() returns (E_corr mean, variance)."""
+        Xd = np.ascontiguousarray(Xd, dtype=np.float32)
+        Xo = np.ascontiguousarray(Xo, dtype=np.float32)
+        energy = np.zeros(2, dtype=np.float64)
+        tk = ctypes.c_uint64()
+        self.check(self.lib.gp_server_molecule(
+            self.h, diag_id, Xd.ctypes.data_as(ctypes.c_void_p), Xd.shape[0], off_id,
+            Xo.ctypes.data_as(ctypes.c_void_p) if Xo.shape[0] else None, Xo.shape[0],
+            energy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(tk)))
+        self._keep[tk.value] = (Xd, energy, Xo)
         return tk.value
 
     def solve(self, X: np.ndarray, theta: Theta, y: np.ndarray, k: int = 32, tol: float = 1e-4,
@@ -378,7 +428,9 @@ class Server:
         if rc == _lib.GP_ETIMEOUT:
             return rc, None, None
         kept = self._keep.pop(ticket, None)
-        out = None if kept is None else kept[1] if len(kept) == 2 else kept[2]
+        out = None if kept is None else kept[1] if len(kept) <= 3 else kept[2]
+        if isinstance(out, np.ndarray) and out.dtype == np.float64 and out.shape == (2,):
+            out = (float(out[0]), float(out[1]))
         return rc, lat.value, out
 
     def stats(self):

@@ -23,6 +23,8 @@ constexpr int kRedBlocks = 304;   // row chunks of the two-stage reductions (2 p
 
 struct CgScal {
   double rz, rz_new, dw, bnorm, relres, alpha, beta;
+  double tol;      // this column's stop tolerance on the recurrence residual
+  double true_prev;  // last measured true relative residual (true-residual checks)
   int active, iters;
 };
 
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(256, NC == 16 ? 2 : 1) z64_apply_kernel(const 
 
 // ---- CG scalar kernels -------------------------------------------------------
 __global__ void cg_init_kernel(CgScal* sc, const double* __restrict__ bb,
-                               const double* __restrict__ rzpart, int nblk, int t,
+                               const double* __restrict__ rzpart, int nblk, int t, double tol,
                                double* __restrict__ rz0, int* iters,
                                double* relres, int* nact) {
   if (threadIdx.x == 0) *nact = 0;
@@ -361,6 +363,8 @@ __global__ void cg_init_kernel(CgScal* sc, const double* __restrict__ bb,
     s.dw = 0.0;
     s.alpha = 0.0;
     s.beta = 0.0;
+    s.tol = tol;
+    s.true_prev = 1e300;
     s.active = s.bnorm > 0.0 ? 1 : 0;
     s.relres = s.active ? 1.0 : 0.0;
     s.iters = 0;
@@ -373,11 +377,12 @@ __global__ void cg_init_kernel(CgScal* sc, const double* __restrict__ bb,
 }
 
 __global__ void cg_alpha_kernel(CgScal* sc, const double* __restrict__ dwpart,
-                                int nblk, int t, int it, double* __restrict__ ah,
+                                int nblk, int t, double* __restrict__ ah,
                                 int* flags) {
   for (int c = threadIdx.x; c < t; c += blockDim.x) {
     CgScal s = sc[c];
     double a = 0.0;
+    const bool was_active = s.active != 0;
     if (s.active) {
       double dw = 0.0;
       for (int b = 0; b < nblk; ++b) dw += dwpart[(int64_t)c * nblk + b];
@@ -391,7 +396,10 @@ __global__ void cg_alpha_kernel(CgScal* sc, const double* __restrict__ dwpart,
     }
     s.alpha = a;
     sc[c] = s;
-    ah[(int64_t)it * t + c] = a;
+    // each column's coefficients are contiguous from its own step 0, so a
+    // column that resumes after a true-residual check (mbcg_run) continues
+    // its own Lanczos sequence without gaps
+    if (was_active) ah[(int64_t)s.iters * t + c] = a;
   }
 }
 
@@ -429,8 +437,7 @@ __global__ void cg_update_kernel(float* __restrict__ U, float* __restrict__ R,
 
 __global__ void cg_check_beta_kernel(CgScal* sc, const double* __restrict__ rrpart,
                                      const double* __restrict__ rzpart, int nblk,
-                                     int t, int it, double tol,
-                                     double* __restrict__ bh, int* iters,
+                                     int t, double* __restrict__ bh, int* iters,
                                      double* relres, int* flags) {
   if (threadIdx.x == 0) flags[0] = 0;
   __syncthreads();
@@ -444,8 +451,8 @@ __global__ void cg_check_beta_kernel(CgScal* sc, const double* __restrict__ rrpa
         rz += rzpart[(int64_t)c * nblk + q];
       }
       s.relres = sqrt(rr) / s.bnorm;
-      s.iters = it + 1;
-      if (s.relres < tol) {
+      s.iters += 1;
+      if (s.relres < s.tol) {
         s.active = 0;
       } else if (!(rz > 0.0) || !isfinite(rz)) {
         atomicOr(flags + 1, 1);
@@ -456,11 +463,96 @@ __global__ void cg_check_beta_kernel(CgScal* sc, const double* __restrict__ rrpa
       }
       if (iters) iters[c] = s.iters;
       if (relres) relres[c] = s.relres;
+      bh[(int64_t)(s.iters - 1) * t + c] = b;
     }
     s.beta = b;
     sc[c] = s;
-    bh[(int64_t)it * t + c] = b;
     if (s.active) atomicAdd(flags, 1);
+  }
+}
+
+// ---- true-residual check (mbcg_run) --------------------------------------------
+// part[c * nblk + b] = sum over rows of block b of (B_c - W_c)^2, W = K-hat U
+__global__ void true_resid_partial_kernel(const float* __restrict__ B, int64_t ldb,
+                                          const float* __restrict__ W, int64_t ldw, int64_t n,
+                                          double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int c = blockIdx.y, nblk = gridDim.x;
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  const float* b = B + (int64_t)c * ldb;
+  const float* w = W + (int64_t)c * ldw;
+  double acc = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const double r = (double)b[i] - (double)w[i];
+    acc += r * r;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(int64_t)c * nblk + blockIdx.x] = s;
+}
+
+// Columns c < tc: the measured true relative residual ||B_c - K-hat U_c|| /
+// ||B_c|| goes to true_out[c] (nullable).  A column whose measure is
+// not below `pass` (margin x tol) is re-activated (when `resume`) with its
+// recurrence target lowered in proportion, unless its measure has stopped
+// falling (then it stays stopped); flags[0] counts the columns that did not
+// pass, flags[2] the columns re-activated.
+__global__ void cg_true_mark_kernel(CgScal* sc, const double* __restrict__ part, int nblk, int tc,
+                                    double pass, int resume, double* true_out, int* flags) {
+  if (threadIdx.x == 0) {
+    flags[0] = 0;
+    flags[2] = 0;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < tc; c += blockDim.x) {
+    CgScal s = sc[c];
+    if (!(s.bnorm > 0.0)) continue;
+    double rr = 0.0;
+    for (int q = 0; q < nblk; ++q) rr += part[(int64_t)c * nblk + q];
+    const double tr = sqrt(rr) / s.bnorm;
+    if (true_out) true_out[c] = tr;
+    // a measure that fell by less than a quarter since the last check has
+    // reached the rounding floor of FP32 storage: continuing would not help
+    const bool progress = tr < 0.75 * s.true_prev;
+    s.true_prev = tr;
+    sc[c] = s;
+    if (!(tr < pass)) {
+      atomicAdd(flags, 1);
+      if (resume && progress && isfinite(tr)) {
+        // the recurrence residual tracks the true one up to a rounding gap:
+        // aim the recurrence at the same ratio below its last value, and at
+        // least a factor 2 lower
+        const double ratio = fmin(0.5, 0.9 * pass / tr);
+        s.tol = fmax(s.relres, 1e-300) * ratio;
+        s.active = 1;
+        sc[c] = s;
+        atomicAdd(flags + 2, 1);
+      }
+    }
+  }
+}
+
+// A re-activated column continues its own CG recurrence: Z = P^{-1} R has
+// just been formed, beta = (r.z)/(r_old.z_old) completes the step on which it
+// had stopped (its history entry, left 0, is filled in) and D = Z + beta D
+// follows in cg_dupdate_kernel.
+__global__ void cg_resume_beta_kernel(CgScal* sc, const double* __restrict__ rzpart, int nblk, int t,
+                                      double* __restrict__ bh, int* flags) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    CgScal s = sc[c];
+    if (!s.active) continue;
+    double rz = 0.0;
+    for (int q = 0; q < nblk; ++q) rz += rzpart[(int64_t)c * nblk + q];
+    if (!(rz > 0.0) || !isfinite(rz) || s.iters < 1) {
+      atomicOr(flags + 1, 1);
+      s.active = 0;
+      s.beta = 0.0;
+    } else {
+      s.beta = rz / s.rz;
+      s.rz = rz;
+      bh[(int64_t)(s.iters - 1) * t + c] = s.beta;
+    }
+    sc[c] = s;
   }
 }
 
@@ -650,6 +742,7 @@ int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res) {
   const Prep& p = *a.prep;
   const int64_t n = p.n, ld = p.n_pad;
   const int t = a.t;
+  const int tc = std::min(std::max(a.true_cols, 0), t);
   float* R = ws<float>(ctx, WS_CG_R, (size_t)ld * t);
   float* Z = ws<float>(ctx, WS_CG_Z, (size_t)ld * t);
   float* D = ws<float>(ctx, WS_CG_D, (size_t)ld * t);
@@ -670,9 +763,9 @@ int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res) {
   GP_TRY(copy_vectors(ctx, a.B, a.ldb, R, ld, n, t, 1.f));
   GP_TRY(copy_vectors(ctx, nullptr, 0, a.U, a.ldu, n, t, 0.f));
   GP_TRY(dot_columns(ctx, R, R, ld, n, t, bb));
-  GP_CUDA(ctx, cudaMemsetAsync(dflags, 0, 2 * sizeof(int), ctx->stream));
+  GP_CUDA(ctx, cudaMemsetAsync(dflags, 0, 3 * sizeof(int), ctx->stream));
   GP_TRY(precond_apply_impl(ctx, a.pc, n, R, Z, ld, t, nullptr, p_rz));
-  cg_init_kernel<<<1, 256, 0, ctx->stream>>>(sc, bb, p_rz, kRedBlocks, t, a.rz0,
+  cg_init_kernel<<<1, 256, 0, ctx->stream>>>(sc, bb, p_rz, kRedBlocks, t, a.tol, a.rz0,
                                              a.iters_dev, a.relres_dev, dflags);
   GP_LAUNCHED(ctx);
   GP_TRY(copy_vectors(ctx, Z, ld, D, ld, n, t, 1.f));
@@ -684,26 +777,74 @@ int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res) {
   res->iters_max = 0;
   res->n_kmv = 0;
   res->breakdown = false;
+  res->true_checks = 0;
+  res->true_ok = tc == 0;
   res->converged = flags[0] == 0;
-  for (int it = 0; it < a.max_iter && flags[0] > 0; ++it) {
-    GP_TRY(kmv(ctx, p, p, D, ld, t, W, ld, a.s, a.sigma2, true, a.precision));
+  // The stop rule (Sec. 4) is on the relative residual ||b - K-hat w|| /
+  // ||b||.  The CG recurrence residual drifts from that true residual by
+  // rounding, so when every column has met tol by its recurrence, the first
+  // tc columns are verified with one K-hat product of the iterate, and a
+  // column whose true residual is not below kTrueMargin x tol continues its
+  // own recurrence to a lower target (its Lanczos coefficients stay one
+  // unbroken sequence).  At most kTrueChecks verifications.
+  constexpr int kTrueChecks = 4;
+  constexpr double kTrueMargin = 0.8;
+  int it = 0;
+  for (;;) {
+    for (; it < a.max_iter && flags[0] > 0; ++it) {
+      GP_TRY(kmv(ctx, p, p, D, ld, t, W, ld, a.s, a.sigma2, true, a.precision));
+      res->n_kmv++;
+      dot_partial_kernel<<<dim3(kRedBlocks, t), 256, 0, ctx->stream>>>(D, W, ld, n, sc, p_dw);
+      GP_LAUNCHED(ctx);
+      cg_alpha_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_dw, kRedBlocks, t, a.alpha_hist, dflags);
+      GP_LAUNCHED(ctx);
+      cg_update_kernel<<<dim3(kRedBlocks, t), 256, 0, ctx->stream>>>(a.U, R, D, W, ld, a.ldu, n, sc, p_rr);
+      GP_LAUNCHED(ctx);
+      GP_TRY(precond_apply_impl(ctx, a.pc, n, R, Z, ld, t, sc, p_rz));
+      cg_check_beta_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_rr, p_rz, kRedBlocks, t, a.beta_hist,
+                                                       a.iters_dev, a.relres_dev, dflags);
+      GP_LAUNCHED(ctx);
+      cg_dupdate_kernel<<<dim3(eg, t), 256, 0, ctx->stream>>>(D, Z, ld, n, sc);
+      GP_LAUNCHED(ctx);
+      GP_CUDA(ctx, cudaMemcpyAsync(flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      GP_TRY(check_status(ctx));
+      res->iters_max = it + 1;
+      if (flags[1]) {
+        res->breakdown = true;
+        break;
+      }
+    }
+    if (res->breakdown || flags[0] > 0 || tc == 0) break;
+    // every column met tol by its recurrence: verify the first tc
+    const bool resume = res->true_checks + 1 < kTrueChecks && it < a.max_iter;
+    GP_TRY(kmv(ctx, p, p, a.U, a.ldu, tc, W, ld, a.s, a.sigma2, true, a.precision));
     res->n_kmv++;
-    dot_partial_kernel<<<dim3(kRedBlocks, t), 256, 0, ctx->stream>>>(D, W, ld, n, sc, p_dw);
+    res->true_checks++;
+    true_resid_partial_kernel<<<dim3(kRedBlocks, tc), 256, 0, ctx->stream>>>(a.B, a.ldb, W, ld, n, p_rr);
     GP_LAUNCHED(ctx);
-    cg_alpha_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_dw, kRedBlocks, t, it, a.alpha_hist, dflags);
+    cg_true_mark_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_rr, kRedBlocks, tc, kTrueMargin * a.tol,
+                                                    resume ? 1 : 0, a.true_dev, dflags);
     GP_LAUNCHED(ctx);
-    cg_update_kernel<<<dim3(kRedBlocks, t), 256, 0, ctx->stream>>>(a.U, R, D, W, ld, a.ldu, n, sc, p_rr);
-    GP_LAUNCHED(ctx);
+    GP_CUDA(ctx, cudaMemcpyAsync(flags, dflags, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    GP_TRY(check_status(ctx));
+    if (flags[0] == 0) {
+      res->true_ok = true;
+      break;
+    }
+    // flags[0] > 0 columns above the margin: reported as not converged
+    // unless some were re-activated and now pass
+    if (!resume || flags[2] == 0) break;
+    flags[0] = flags[2];
+    // continue the re-activated columns' recurrences
     GP_TRY(precond_apply_impl(ctx, a.pc, n, R, Z, ld, t, sc, p_rz));
-    cg_check_beta_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_rr, p_rz, kRedBlocks, t, it, a.tol,
-                                                     a.beta_hist, a.iters_dev, a.relres_dev, dflags);
+    cg_resume_beta_kernel<<<1, 256, 0, ctx->stream>>>(sc, p_rz, kRedBlocks, t, a.beta_hist, dflags);
     GP_LAUNCHED(ctx);
     cg_dupdate_kernel<<<dim3(eg, t), 256, 0, ctx->stream>>>(D, Z, ld, n, sc);
     GP_LAUNCHED(ctx);
-    GP_CUDA(ctx, cudaMemcpyAsync(flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GP_CUDA(ctx, cudaMemcpyAsync(flags + 1, dflags + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    GP_TRY(check_status(ctx));
-    res->iters_max = it + 1;
     if (flags[1]) {
       res->breakdown = true;
       break;

@@ -124,6 +124,35 @@ int prep_train(gp_ctx* ctx, const float* X, int64_t N, int d,
 }
 
 bool valid_precision(int p) { return p >= GP_FP32_PLAIN && p <= GP_TF32; }
+bool valid_stop(int r) { return r == GP_STOP_RECURRENCE || r == GP_STOP_TRUE; }
+
+__global__ void fill_one_kernel(float* __restrict__ v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = 1.f;
+}
+
+int fill_one(gp_ctx* ctx, float* v, int64_t n) {
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 1024));
+  fill_one_kernel<<<g, 256, 0, ctx->stream>>>(v, n);
+  GP_LAUNCHED(ctx);
+  return GP_OK;
+}
+
+// the model's preconditioner P = L L^T + D (FP32 factor copy and D^{-1/2})
+Precond model_precond(const gp_model* m) {
+  Precond pc;
+  pc.k = m->k;
+  pc.n = m->n;
+  pc.L = m->L;
+  pc.L32 = m->L32;
+  pc.ld32 = m->n_pad;
+  pc.cfac = m->cfac;
+  pc.cinv = m->cfac ? m->cfac + (size_t)m->k * m->k : nullptr;
+  pc.dh = m->dh;
+  pc.logdet = m->pc_logdet;
+  pc.sigma2 = m->sigma2;
+  return pc;
+}
 
 }  // namespace
 }  // namespace gp
@@ -182,6 +211,18 @@ const char* gp_last_error(const gp_ctx* ctx) {
 }
 
 int64_t gp_launch_count(const gp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int gp_set_option(gp_ctx* ctx, int option, int value) {
+  if (!ctx) return GP_EINVAL;
+  switch (option) {
+    case GP_OPT_SYMMETRIC_KMV:
+      if (value != 0 && value != 1) return set_err(ctx, GP_EINVAL, "gp_set_option: value must be 0 or 1");
+      ctx->sym_kmv = value != 0;
+      return GP_OK;
+    default:
+      return set_err(ctx, GP_EINVAL, "gp_set_option: unknown option %d", option);
+  }
+}
 
 int gp_profile(gp_ctx* ctx, int enable) {
   if (!ctx) return GP_EINVAL;
@@ -250,12 +291,12 @@ int gp_pivchol(gp_ctx* ctx, const float* X, int64_t N, int d,
 int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
             const gp_theta* theta, const double* L, int k,
             const double* resid_diag, const float* B,
-            int t, double tol, int max_iter, int precision, float* Omega,
+            int t, double tol, int max_iter, int stop_rule, int precision, float* Omega,
             double* alpha_hist, double* beta_hist, int* iters,
             double* rel_resid) {
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!B || !Omega || t < 1 || t > kMaxT || max_iter < 1 || !(tol >= 0.0) ||
-      k < 0 || (k > 0 && !L) || !valid_precision(precision))
+      k < 0 || (k > 0 && !L) || !valid_precision(precision) || !valid_stop(stop_rule))
     return set_err(ctx, GP_EINVAL, "gp_mbcg: bad arguments");
   Prep p;
   GP_TRY(prep_train(ctx, X, N, d, theta, precision, &p));
@@ -283,6 +324,8 @@ int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
   a.beta_hist = bh;
   a.iters_dev = iters_dev;
   a.relres_dev = rr_dev;
+  a.true_cols = stop_rule == GP_STOP_TRUE ? t : 0;
+  a.true_dev = rr_dev;   // rel_resid reports the verified true residuals
   CgResult res;
   GP_TRY(mbcg_run(ctx, a, &res));
   if (iters || rel_resid) {
@@ -296,7 +339,12 @@ int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
     if (rel_resid) std::memcpy(rel_resid, h + sizeof(int) * ((t + 1) & ~1), sizeof(double) * t);
   }
   if (res.breakdown) return set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown (loss of definiteness)");
-  if (!res.converged) return set_err(ctx, GP_ENOTCONV, "mBCG: max_iter=%d reached", max_iter);
+  if (!res.converged)
+    return set_err(ctx, GP_ENOTCONV,
+                   res.true_checks > 0 && !res.true_ok
+                       ? "mBCG: true residual above tol after %d verifications"
+                       : "mBCG: max_iter=%d reached",
+                   res.true_checks > 0 && !res.true_ok ? res.true_checks : max_iter);
   return GP_OK;
 }
 
@@ -410,7 +458,9 @@ int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
       const double prev = rel[c];
       rel[c] = std::sqrt(h[c]) / bnorm[c];
       if (rel[c] < 0.9 * prev) progress = true;
-      if (rel[c] < tol) {
+      // the measured residual carries the outer product's own error: a
+      // column passes below 0.8 tol, the margin of GP_STOP_TRUE
+      if (rel[c] < 0.8 * tol) {
         done[c] = 1;
         // a stopped column's residual is not refined further
         GP_CUDA(ctx, cudaMemsetAsync(R + (size_t)c * N, 0, sizeof(float) * N, st));
@@ -435,11 +485,11 @@ int gp_mbcg_refine(gp_ctx* ctx, const float* X, int64_t N, int d,
 int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
                       const gp_theta* theta, const float* y, int n_probes,
                       uint64_t seed, int k, int precond, double tol, int max_iter,
-                      int precision, double* logml, double* logdet,
+                      int stop_rule, int precision, double* logml, double* logdet,
                       double* grad, double* logdet_stderr, gp_stats* stats) {
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!y || n_probes < 1 || n_probes > 255 || k < 0 || k > N || max_iter < 1 ||
-      !(tol >= 0.0) || !logml || !logdet || !valid_precision(precision) ||
+      !(tol >= 0.0) || !logml || !logdet || !valid_precision(precision) || !valid_stop(stop_rule) ||
       (precond != GP_PC_SIGMA && precond != GP_PC_RESID))
     return set_err(ctx, GP_EINVAL, "gp_logml_and_grad: bad arguments");
   const double s = theta->outputscale, sig2 = theta->sigma2;
@@ -475,6 +525,7 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
   double* dots = Gacc + 512;                               // T1 + 1
   int* iters = reinterpret_cast<int*>(dots + 512);         // T1
   int* bad = iters + 256;
+  double* truer = reinterpret_cast<double*>(iters + 512);  // 1: y's true residual
   GP_CUDA(ctx, cudaMemsetAsync(B, 0, sizeof(float) * ld * T1, ctx->stream));
   GP_CUDA(ctx, cudaMemsetAsync(U, 0, sizeof(float) * ld * T1, ctx->stream));
   GP_CUDA(ctx, cudaMemsetAsync(Z0, 0, sizeof(float) * ld * T1, ctx->stream));
@@ -501,6 +552,8 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
   a.rz0 = rz0;
   a.iters_dev = iters;
   a.relres_dev = relres;
+  a.true_cols = stop_rule == GP_STOP_TRUE ? 1 : 0;   // y's column: the solve a = K-hat^{-1} y
+  a.true_dev = truer;
   CgResult res;
   GP_TRY(mbcg_run(ctx, a, &res));
   if (res.breakdown) return set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown (loss of definiteness)");
@@ -532,6 +585,7 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
   const double* h_dots = h_G + 512;
   const int* h_iters = reinterpret_cast<const int*>(h_dots + 512);
   const int h_bad = h_iters[256];
+  const double h_true = *reinterpret_cast<const double*>(h_iters + 512);
   if (h_bad) return set_err(ctx, GP_EBREAKDOWN, "Lanczos tridiagonal not positive definite (%d)", h_bad);
   double acc = 0.0, acc2 = 0.0;
   for (int c = 1; c <= n_probes; ++c) {
@@ -568,16 +622,22 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
     stats->relres_max = rm;
     stats->logdet_P = pc.logdet;
     stats->yKinvy = yKy;
+    stats->true_relres_y = res.true_checks > 0 ? h_true : -1.0;
+    stats->true_checks = res.true_checks;
   }
-  if (!res.converged) return set_err(ctx, GP_ENOTCONV, "mBCG: max_iter=%d reached", max_iter);
+  if (!res.converged)
+    return set_err(ctx, GP_ENOTCONV,
+                   res.true_checks > 0 && !res.true_ok ? "mBCG: y's true residual above tol after %d verifications"
+                                                        : "mBCG: max_iter=%d reached",
+                   res.true_checks > 0 && !res.true_ok ? res.true_checks : max_iter);
   return GP_OK;
 }
 
 int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
                  const gp_theta* theta, const float* y, int k, int precond, int block, double tol,
-                 int max_iter, int precision, gp_model** out, gp_stats* stats) {
+                 int max_iter, int stop_rule, int precision, gp_model** out, gp_stats* stats) {
   GP_TRY(check_common(ctx, X, N, d, theta));
-  if (!y || !out || k < 0 || k > N || max_iter < 1 || !valid_precision(precision) ||
+  if (!y || !out || k < 0 || k > N || max_iter < 1 || !valid_precision(precision) || !valid_stop(stop_rule) ||
       (precond != GP_PC_SIGMA && precond != GP_PC_RESID) || block < 1 || block > 32)
     return set_err(ctx, GP_EINVAL, "gp_model_fit: bad arguments");
   *out = nullptr;
@@ -728,6 +788,8 @@ int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
   a.beta_hist = bh;
   a.iters_dev = rec;
   a.relres_dev = reinterpret_cast<double*>(rec + 2);
+  a.true_cols = stop_rule == GP_STOP_TRUE ? 1 : 0;
+  a.true_dev = reinterpret_cast<double*>(rec + 4);
   CgResult res;
   {
     int rc = mbcg_run(ctx, a, &res);
@@ -735,20 +797,27 @@ int gp_model_fit(gp_ctx* ctx, const float* X, int64_t N, int d,
   }
   if (stats) {
     int* h = static_cast<int*>(pinned_get(ctx, 64));
-    GP_CUDA(ctx, cudaMemcpyAsync(h, rec, 16, cudaMemcpyDeviceToHost, st));
+    GP_CUDA(ctx, cudaMemcpyAsync(h, rec, 24, cudaMemcpyDeviceToHost, st));
     GP_CUDA(ctx, cudaStreamSynchronize(st));
     std::memset(stats, 0, sizeof(*stats));
     stats->iters_max = stats->iters_y = h[0];
-    double rr;
+    double rr, tr;
     std::memcpy(&rr, h + 2, sizeof(double));
+    std::memcpy(&tr, h + 4, sizeof(double));
     stats->relres_y = stats->relres_max = rr;
+    stats->true_relres_y = res.true_checks > 0 ? tr : -1.0;
+    stats->true_checks = res.true_checks;
     stats->rank = rank;
     stats->n_kmatmul = res.n_kmv;
     stats->logdet_P = pc.logdet;
   }
   GP_CUDA(ctx, cudaStreamSynchronize(st));
   if (res.breakdown) return fail(set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown"));
-  if (!res.converged) return fail(set_err(ctx, GP_ENOTCONV, "mBCG: max_iter=%d reached", max_iter));
+  if (!res.converged)
+    return fail(set_err(ctx, GP_ENOTCONV,
+                        res.true_checks > 0 && !res.true_ok ? "mBCG: y's true residual above tol after %d verifications"
+                                                             : "mBCG: max_iter=%d reached",
+                        res.true_checks > 0 && !res.true_ok ? res.true_checks : max_iter));
   *out = m;
   return GP_OK;
 }
@@ -760,7 +829,7 @@ void gp_model_free(gp_model* m) {
   for (void* q : {(void*)m->mu, (void*)m->xt, (void*)m->norm, (void*)m->xt_hi,
                   (void*)m->xt_lo, (void*)m->xh_hi, (void*)m->xh_lo, (void*)m->norm_h,
                   (void*)m->xh_scale, (void*)m->alpha,
-                  (void*)m->L, (void*)m->L32, (void*)m->cfac, (void*)m->dh})
+                  (void*)m->L, (void*)m->L32, (void*)m->cfac, (void*)m->dh, (void*)m->love_R})
     if (q) cudaFree(q);
   delete m;
 }
@@ -787,19 +856,13 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, const float* Xp, int64_t M,
   GP_TRY(prepare_features(ctx, Xp, M, m->d, m->mu, m->ell.data(), m->precision, WS_XT2, &q));
   GP_TRY(kmv(ctx, q, mp, m->alpha, m->n_pad, 1, mean, M, m->s, 0.0, false, m->precision));
   if (!var || var_mode == GP_VAR_NONE) return GP_OK;
+  if (var_mode == GP_VAR_CACHED) {
+    if (!m->love_R) return set_err(ctx, GP_EINVAL, "gp_predict: the model has no variance cache");
+    return cached_variance(ctx, m, mp, q, var);
+  }
   if (var_mode != GP_VAR_EXACT) return set_err(ctx, GP_EINVAL, "gp_predict: unknown var_mode");
   // exact latent variance: k(x',x') - k*^T K-hat^{-1} k*, in chunks of RHS
-  Precond pc;
-  pc.k = m->k;
-  pc.n = m->n;
-  pc.L = m->L;
-  pc.L32 = m->L32;
-  pc.ld32 = m->n_pad;
-  pc.cfac = m->cfac;
-  pc.cinv = m->cfac ? m->cfac + (size_t)m->k * m->k : nullptr;
-  pc.dh = m->dh;
-  pc.logdet = m->pc_logdet;
-  pc.sigma2 = m->sigma2;
+  Precond pc = model_precond(m);
   const int CH = 64;
   const int64_t ld = m->n_pad;
   float* Kc = ws<float>(ctx, WS_PR_K, (size_t)ld * CH);
@@ -846,6 +909,121 @@ int gp_predict(gp_ctx* ctx, const gp_model* m, const float* Xp, int64_t M,
   }
   GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (notconv) return set_err(ctx, GP_ENOTCONV, "variance solves reached max_iter");
+  return GP_OK;
+}
+
+int gp_model_variance_cache(gp_ctx* ctx, gp_model* m, const float* b, int rank, int* rank_out) {
+  if (!ctx || !m || rank < 1 || rank > GP_VAR_CACHE_MAX_RANK || rank > m->n || !rank_out)
+    return set_err(ctx, GP_EINVAL, "gp_model_variance_cache: bad arguments (1 <= rank <= %d)",
+                   GP_VAR_CACHE_MAX_RANK);
+  if (m->device != ctx->device) return set_err(ctx, GP_EINVAL, "gp_model_variance_cache: model on another device");
+  GP_CUDA(ctx, cudaSetDevice(ctx->device));
+  const Prep mp = model_prep_of(m);
+  const float* start = b;
+  if (!start) {
+    // start at K-hat a, which is y up to the fit's tolerance
+    float* kb = ws<float>(ctx, WS_LV_C, (size_t)m->n_pad);
+    if (!kb) return set_err(ctx, GP_ENOMEM, "workspace (variance cache)");
+    GP_TRY(kmv(ctx, mp, mp, m->alpha, m->n_pad, 1, kb, m->n_pad, m->s, m->sigma2, true, m->precision));
+    start = kb;
+  }
+  float* R = nullptr;
+  if (cudaMalloc(&R, sizeof(float) * (size_t)m->n_pad * rank) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, GP_ENOMEM, "variance cache allocation");
+  }
+  int k = 0;
+  const int rc = lanczos_cache_build(ctx, mp, m->s, m->sigma2, m->precision, start, rank, R, &k);
+  if (rc != GP_OK) {
+    cudaFree(R);
+    return rc;
+  }
+  if (m->love_R) cudaFree(m->love_R);
+  m->love_R = R;
+  m->love_m = k;
+  *rank_out = k;
+  return GP_OK;
+}
+
+int gp_predict_sum(gp_ctx* ctx, const gp_model* m, const float* Xp, int64_t M, double* mean_sum,
+                   double* var_sum, int var_mode) {
+  if (!ctx || !m || !Xp || M <= 0 || !mean_sum ||
+      (var_sum && var_mode != GP_VAR_EXACT && var_mode != GP_VAR_CACHED))
+    return set_err(ctx, GP_EINVAL, "gp_predict_sum: bad arguments");
+  if (m->device != ctx->device) return set_err(ctx, GP_EINVAL, "gp_predict_sum: model on another device");
+  if (var_sum && var_mode == GP_VAR_CACHED && !m->love_R)
+    return set_err(ctx, GP_EINVAL, "gp_predict_sum: the model has no variance cache");
+  GP_CUDA(ctx, cudaSetDevice(ctx->device));
+  const Prep mp = model_prep_of(m);
+  Prep q;
+  GP_TRY(prepare_features(ctx, Xp, M, m->d, m->mu, m->ell.data(), m->precision, WS_XT2, &q));
+  const int kc = var_mode == GP_VAR_CACHED ? m->love_m : 0;
+  // sums: [0] the means, [1] 1^T K(X',X') 1, [2] c^T K-hat^{-1} c, [3..] R^T c
+  double* sums = ws<double>(ctx, WS_LV_P, (size_t)4 + kc);
+  float* mb = ws<float>(ctx, WS_LV_M, (size_t)std::max<int64_t>(M, 1));
+  if (!sums || !mb) return set_err(ctx, GP_ENOMEM, "workspace (predict sum)");
+  GP_CUDA(ctx, cudaMemsetAsync(sums, 0, sizeof(double) * (4 + kc), ctx->stream));
+  GP_TRY(kmv(ctx, q, mp, m->alpha, m->n_pad, 1, mb, M, m->s, 0.0, false, m->precision));
+  GP_TRY(row_sums(ctx, mb, M, 1, M, sums));
+  if (var_sum) {
+    GP_TRY(block_ksum(ctx, q, m->s, sums + 1));
+    if (var_mode == GP_VAR_CACHED) {
+      float* KR = ws<float>(ctx, WS_LV_K, (size_t)kc * M);
+      if (!KR) return set_err(ctx, GP_ENOMEM, "workspace (predict sum)");
+      GP_TRY(kmv(ctx, q, mp, m->love_R, m->n_pad, kc, KR, M, m->s, 0.0, false, m->precision));
+      GP_TRY(row_sums(ctx, KR, M, kc, M, sums + 4));
+    } else {
+      // c = K(X, X') 1, then c^T K-hat^{-1} c by preconditioned CG
+      const int64_t ld = m->n_pad;
+      float* ones = mb;
+      float* cv = ws<float>(ctx, WS_LV_C, (size_t)ld);
+      float* wv = ws<float>(ctx, WS_LV_W, (size_t)ld);
+      double* ah = ws<double>(ctx, WS_CG_AH, (size_t)m->max_iter);
+      double* bh = ws<double>(ctx, WS_CG_BH, (size_t)m->max_iter);
+      char* rec = static_cast<char*>(ws_get(ctx, WS_GR_ACC, 256));
+      if (!cv || !wv || !ah || !bh || !rec) return set_err(ctx, GP_ENOMEM, "workspace (predict sum)");
+      GP_TRY(fill_one(ctx, ones, M));
+      GP_CUDA(ctx, cudaMemsetAsync(cv, 0, sizeof(float) * ld, ctx->stream));
+      GP_TRY(kmv(ctx, mp, q, ones, M, 1, cv, ld, m->s, 0.0, false, m->precision));
+      Precond pc = model_precond(m);
+      CgArgs a;
+      a.prep = &mp;
+      a.s = m->s;
+      a.sigma2 = m->sigma2;
+      a.pc = &pc;
+      a.B = cv;
+      a.ldb = ld;
+      a.t = 1;
+      a.tol = m->tol;
+      a.max_iter = m->max_iter;
+      a.precision = m->precision;
+      a.U = wv;
+      a.ldu = ld;
+      a.alpha_hist = ah;
+      a.beta_hist = bh;
+      a.iters_dev = reinterpret_cast<int*>(rec);
+      a.relres_dev = reinterpret_cast<double*>(rec + 16);
+      CgResult res;
+      GP_TRY(mbcg_run(ctx, a, &res));
+      if (res.breakdown) return set_err(ctx, GP_EBREAKDOWN, "mBCG breakdown (predict sum)");
+      if (!res.converged) return set_err(ctx, GP_ENOTCONV, "predict sum: the solve reached max_iter");
+      GP_TRY(dot_columns(ctx, cv, wv, ld, m->n, 1, sums + 2));
+    }
+  }
+  double* h = static_cast<double*>(pinned_get(ctx, sizeof(double) * (4 + kc)));
+  if (!h) return set_err(ctx, GP_ENOMEM, "pinned staging");
+  GP_CUDA(ctx, cudaMemcpyAsync(h, sums, sizeof(double) * (4 + kc), cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  GP_TRY(check_status(ctx));
+  *mean_sum = h[0];
+  if (var_sum) {
+    double quad = h[2];
+    if (var_mode == GP_VAR_CACHED) {
+      quad = 0.0;
+      for (int j = 0; j < kc; ++j) quad += h[4 + j] * h[4 + j];
+    }
+    *var_sum = h[1] - quad;
+  }
   return GP_OK;
 }
 

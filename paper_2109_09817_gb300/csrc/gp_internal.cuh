@@ -53,6 +53,7 @@ enum WsSlot {
   WS_RF_R, WS_RF_D, WS_RF_W, WS_RF_S, WS_GT_P, WS_GT_T,
   WS_BC_C, WS_BC_P, WS_BC_W, WS_BC_S, WS_BC_R, WS_BC_RH, WS_BC_D, WS_BC_D2, WS_BC_DT,
   WS_BC_WK, WS_BC_Q, WS_BC_OM, WS_BC_M, WS_BC_DH, WS_PC_DH64, WS_CG_W64,
+  WS_LV_W, WS_LV_P, WS_LV_T, WS_LV_K, WS_LV_M, WS_LV_C,
   WS_COUNT
 };
 
@@ -88,6 +89,8 @@ struct gp_model {
   double* cfac = nullptr;
   float* dh = nullptr;         // D^{-1/2}, n_pad
   double pc_logdet = 0.0;
+  float* love_R = nullptr;     // variance cache R = Q C^{-T}: love_m vectors, ld n_pad
+  int love_m = 0;
 };
 
 struct gp_ctx {
@@ -105,6 +108,7 @@ struct gp_ctx {
   size_t ev_used = 0;
   double prof_flops = 0.0, prof_elems = 0.0;
   bool status_init = false;      // device status word (bounded-wait timeouts)
+  bool sym_kmv = true;           // symmetric split-FP16 K-hat V (gp_set_option)
   int* status_host = nullptr;    // its own pinned word (never the staging area)
 };
 
@@ -193,6 +197,15 @@ int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V,
            int64_t ldv, int t, float* out, int64_t ldo, float s, bool sym,
            int precision);
 bool kmv_tc_supported(const Prep& rows, int t, int precision);
+// Symmetric split-FP16 product (kmv_sym.cu): rows and columns are the same
+// point set; V already split into FP16 hi/lo parts (T = 16 or 32 padded
+// vectors of length n_pad, leading dimension vld) with per-vector factors vsc.
+int kmv_sym_f16(gp_ctx* ctx, const Prep& p, const __half* vhi, const __half* vlo, const float* vsc,
+                int64_t vld, int t, int T, float* out, int64_t ldo, float s, int* status);
+// kernel entries the symmetric product forms for n points (whole tiles)
+double kmv_sym_entries(int64_t n);
+// whether kmv() takes the symmetric kernel for these arguments
+bool kmv_uses_sym(const gp_ctx* ctx, const Prep& rows, const Prep& cols, bool sym, int precision);
 // Device status word written by kernels whose waits are bounded (0 = ok,
 // GP_ETIMEOUT = a wait gave up).  check_status synchronises, returns the
 // recorded code as a gp error and clears it.
@@ -230,6 +243,8 @@ struct CgResult {
   int n_kmv = 0;
   bool converged = false;
   bool breakdown = false;
+  int true_checks = 0;   // K-hat products spent verifying true residuals
+  bool true_ok = false;  // every verified column passed
 };
 struct CgArgs {
   const Prep* prep = nullptr;
@@ -248,7 +263,12 @@ struct CgArgs {
   float* Z0 = nullptr;           // optional: P^{-1} B out (ld n_pad)
   double* rz0 = nullptr;         // optional device t: r0^T z0
   int* iters_dev = nullptr;      // device t
-  double* relres_dev = nullptr;  // device t
+  double* relres_dev = nullptr;  // device t (true residual for the verified columns)
+  // the first true_cols columns must meet tol by their true relative
+  // residual ||B_c - K-hat U_c|| / ||B_c||, measured with one product of the
+  // iterate once the recurrence has converged (0: recurrence only)
+  int true_cols = 0;
+  double* true_dev = nullptr;    // optional device true_cols: last measured true residuals
 };
 int mbcg_run(gp_ctx* ctx, const CgArgs& a, CgResult* res);
 // Block CG on S^T K-hat S (AltBBMM, bcg.cu): B, Omega t <= 32 vectors (ld
@@ -278,6 +298,16 @@ int grad_tiles(gp_ctx* ctx, const Prep& p, const float* U, const float* W,
                int T1, double* G, double* gs, int precision);
 bool grad_tc_supported(const Prep& p, int T1);
 int grad_tc(gp_ctx* ctx, const Prep& p, const float* U, const float* W, int T1, double* G);
+
+// ---- serving variances (love.cu) ---------------------------------------------------
+int lanczos_cache_build(gp_ctx* ctx, const Prep& p, double s, double sigma2, int precision, const float* b,
+                        int m, float* Q, int* m_out);
+int cached_variance(gp_ctx* ctx, const gp_model* m, const Prep& mp, const Prep& q, float* var);
+int block_ksum(gp_ctx* ctx, const Prep& q, double s, double* sums);
+int row_sums(gp_ctx* ctx, const float* A, int64_t lda, int k, int64_t M, double* sums);
+Prep model_prep_of(const gp_model* m);
+int serve_batch(gp_ctx* ctx, const gp_model* m, const float* Xp, int64_t rows, float* mean, float* var, int nseg,
+                const int64_t* seg, double* sums, int64_t max_part_rows);
 
 // ---- small helpers (cg.cu) ------------------------------------------------------
 // out[c] = sum_a A[c*ld + a] * B[c*ld + a] in FP64, c < t (device doubles)

@@ -263,7 +263,8 @@ int kmv(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V,
     e1 = ctx->ev[ctx->ev_used].second;
     ctx->ev_used++;
     ctx->prof_flops += 2.0 * (double)rows.n * (double)cols.n * (double)(rows.d + t);
-    ctx->prof_elems += (double)rows.n * (double)cols.n;
+    ctx->prof_elems += kmv_uses_sym(ctx, rows, cols, sym, precision) ? kmv_sym_entries(rows.n)
+                                                                 : (double)rows.n * (double)cols.n;
   }
   GP_TRY(kmv_init_out(ctx, sym ? V : nullptr, ldv, t, rows.n, out, ldo, (float)sigma2));
   if (e0) GP_CUDA(ctx, cudaEventRecord(e0, ctx->stream));

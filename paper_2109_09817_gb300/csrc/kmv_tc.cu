@@ -708,6 +708,11 @@ int launch_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const void* vhi, 
 
 }  // namespace
 
+bool kmv_uses_sym(const gp_ctx* ctx, const Prep& rows, const Prep& cols, bool sym, int precision) {
+  return ctx->sym_kmv && sym && precision == GP_FP32_SPLIT_F16 && rows.xh_hi != nullptr && rows.xh_hi == cols.xh_hi &&
+         rows.n == cols.n;
+}
+
 bool kmv_tc_supported(const Prep& rows, int t, int precision) {
   (void)t;
   if (precision == GP_FP32_SPLIT_F16) return rows.xh_hi != nullptr && rows.d_pad <= kHalfCols;
@@ -772,10 +777,13 @@ int kmv_tc(gp_ctx* ctx, const Prep& rows, const Prep& cols, const float* V, int6
       GP_LAUNCHED(ctx);
       split_vh_kernel<<<g, 256, 0, ctx->stream>>>(Vc, ldv, tc, cols.n, T, npad, vmax, vhi, vlo, vsc);
       GP_LAUNCHED(ctx);
-      rc = T == 16 ? launch_tc<kHalfCols, 16, 2>(ctx, rows, cols, vhi, vlo, nullptr, vsc, npad, tc, oc, ldo, s,
-                                                 sym, status)
-                   : launch_tc<kHalfCols, 32, 2>(ctx, rows, cols, vhi, vlo, nullptr, vsc, npad, tc, oc, ldo, s,
-                                                 sym, status);
+      if (kmv_uses_sym(ctx, rows, cols, sym, precision))
+        rc = kmv_sym_f16(ctx, rows, vhi, vlo, vsc, npad, tc, T, oc, ldo, s, status);
+      else
+        rc = T == 16 ? launch_tc<kHalfCols, 16, 2>(ctx, rows, cols, vhi, vlo, nullptr, vsc, npad, tc, oc, ldo, s,
+                                                   sym, status)
+                     : launch_tc<kHalfCols, 32, 2>(ctx, rows, cols, vhi, vlo, nullptr, vsc, npad, tc, oc, ldo, s,
+                                                   sym, status);
       if (rc != GP_OK) return rc;
       continue;
     }

@@ -4,11 +4,12 @@
 
 Workload (synthetic stand-in for MOB-ML pair energies, Sec. 2.1): a diagonal
 model and an off-diagonal model (d = 64 clustered features, fitted through the
-server: split-TF32 mBCG, rank-k residual-diagonal preconditioner).  A
-"molecule" request has n_occ ~ U{2..60} occupied orbitals and asks for the
-predictive mean of its n_occ diagonal and n_occ (n_occ - 1) / 2 off-diagonal
-pair features (one predict request per model, submitted together; the
-molecule's latency is the later of the two).  A fraction of the requests are
+server: split-FP16 mBCG, rank-k residual-diagonal preconditioner, and a
+rank-r Lanczos variance cache each).  A molecule request has n_occ ~ U{2..60}
+occupied orbitals: its n_occ diagonal and n_occ (n_occ - 1) / 2 off-diagonal
+pair features go to the two models in one gp_server_molecule call, which
+returns the correlation energy (the sum of the pair predictions) and the
+variance of that sum.  A fraction of the requests are
 solve requests (a new model's alpha) with N ~ logU[1e3, 2e5] drawn from a pool
 of pre-generated problems.
 
@@ -42,6 +43,8 @@ def main():
     ap.add_argument("--offdiag-n", type=int, default=1 << 20)
     ap.add_argument("--diag-n", type=int, default=65536)
     ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--var-rank", type=int, default=64)
+    ap.add_argument("--precision", default="split_f16")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--fracs", default="0.5,0.8")
     ap.add_argument("--solve-frac", type=float, default=0.1)
@@ -67,19 +70,23 @@ def main():
         th = gp.Theta(w.lengthscale, w.outputscale, w.sigma2)
         t0 = time.perf_counter()
         mid = srv.add_model(torch.from_numpy(w.X).cuda(), th, torch.from_numpy(w.y).cuda(), k=a.k,
-                            tol=1e-4, max_iter=400)
+                            tol=1e-4, max_iter=400, precision=gp.PRECISIONS[a.precision],
+                            var_rank=a.var_rank)
         out[f"fit_{name}_s"] = time.perf_counter() - t0
         models.append((mid, w))
     torch.cuda.synchronize()
 
     def molecule():
         n = int(rng.integers(2, 61))
-        reqs = []
+        rows = []
         for (mid, w), m in zip(models, (n, n * (n - 1) // 2)):
-            rows = rng.integers(0, w.N, size=m)
-            xp = w.X[rows] + rng.normal(0.0, 0.05, size=(m, w.d)).astype(np.float32)
-            reqs.append((mid, xp.astype(np.float32)))
-        return n, reqs
+            idx = rng.integers(0, w.N, size=m)
+            xp = w.X[idx] + rng.normal(0.0, 0.05, size=(m, w.d)).astype(np.float32)
+            rows.append(xp.astype(np.float32))
+        return n, rows
+
+    def submit_molecule(rows):
+        return srv.molecule(models[0][0], rows[0], models[1][0], rows[1])
 
     # solve pool: log-uniform sizes
     sizes = np.exp(rng.uniform(np.log(1e3), np.log(a.solve_nmax), size=a.solve_pool)).astype(int)
@@ -91,10 +98,9 @@ def main():
     # closed-loop predict saturation
     mols = [molecule() for _ in range(200)]
     t0 = time.perf_counter()
-    tks = [[srv.predict(mid, xp) for mid, xp in reqs] for _, reqs in mols]
+    tks = [submit_molecule(rows) for _, rows in mols]
     for tk in tks:
-        for t in tk:
-            assert srv.wait(t)[0] == 0
+        assert srv.wait(tk)[0] == 0
     sp = len(mols) / (time.perf_counter() - t0)
     pairs = sum(n + n * (n - 1) // 2 for n, _ in mols)
     out["predict_saturation_molecules_per_s"] = sp
@@ -167,8 +173,8 @@ def main():
                 tks = [srv.solve(w.X, th, w.y, k=min(a.k, w.N), tol=1e-4, max_iter=400)]
                 n = 0
             else:
-                n, reqs = payload
-                tks = [srv.predict(mid, xp) for mid, xp in reqs]
+                n, rows = payload
+                tks = [submit_molecule(rows)]
                 served_pairs += n + n * (n - 1) // 2
             with lock:
                 pending.append((kind, tks, n))

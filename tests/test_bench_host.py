@@ -23,23 +23,38 @@ def test_split_forms_count_three_products():
     assert bench.tensor_flops_per_entry("tf32", 64, 16) == 160.0
 
 
-def test_roofline_peak_follows_the_operand_type():
-    ent = 1.0e12
-    f16 = bench.roofline("split_f16", 64, 16, ent, 2070.0, PEAKS, "test")
-    tf32 = bench.roofline("split_tf32", 64, 16, ent, 2070.0, PEAKS, "test")
+def test_roofline_is_algorithmic_work_over_sustained_peak():
+    # N = 2^20, d = 64, t = 16: 2 N^2 (d + t) = 1.759e14 flops per product
+    n, ms = 1 << 20, 500.0
+    f16 = bench.roofline("split_f16", 64, 16, n, ms, float(n) ** 2, 2070.0, PEAKS, "test")
+    tf32 = bench.roofline("split_tf32", 64, 16, n, ms, float(n) ** 2, 2070.0, PEAKS, "test")
+    alg = 2.0 * n * n * 80 / 0.5 / 1e12
     assert f16["bound"] == tf32["bound"] == "tensor"
-    assert f16["achieved"] == pytest.approx(480.0)          # 1e12 x 480 / 1e12
-    assert f16["peak"] == pytest.approx(2000.0)             # FP16 = BF16 dense rate
-    assert tf32["peak"] == pytest.approx(2000.0 * 1.1 / 2.25)
-    assert f16["frac"] == pytest.approx(480.0 / 2000.0)
-    assert tf32["frac"] == pytest.approx(2 * f16["frac"] * 2.25 / 2.2)
+    assert f16["achieved"] == pytest.approx(alg)
+    assert f16["peak"] == pytest.approx(1700.0)                 # FP16 = BF16 sustained
+    assert tf32["peak"] == pytest.approx(1700.0 * 1.1 / 2.25)
+    assert f16["frac"] == pytest.approx(alg / 1700.0)
+    # the tensor pipe's own work (3 products per split form) is reported apart
+    assert f16["pipe_tflops"] == pytest.approx(480.0 * n * n / 0.5 / 1e12)
+
+
+def test_sfu_bound_counts_evaluated_entries():
+    n = 1 << 20
+    full = bench.roofline("split_f16", 64, 16, n, 100.0, float(n) ** 2, 2000.0, PEAKS, "test")
+    half = bench.roofline("split_f16", 64, 16, n, 100.0, float(n) ** 2 / 2, 2000.0, PEAKS, "test")
+    per = 1.0 / 30 + 1.0 / 15
+    bound_ms = float(n) ** 2 * per / (152 * 2000.0e6) * 1e3
+    assert full["sfu"]["bound_ms"] == pytest.approx(bound_ms)
+    assert half["sfu"]["bound_ms"] == pytest.approx(bound_ms / 2)
+    assert full["sfu"]["frac"] == pytest.approx(bound_ms / 100.0)
 
 
 def test_roofline_fp32_is_alu_bound():
-    r = bench.roofline("fp32", 64, 16, 1.0e11, 2000.0, PEAKS, "test")
+    n = 65536
+    r = bench.roofline("fp32", 32, 32, n, 20.0, float(n) ** 2, 2000.0, PEAKS, "test")
     assert r["bound"] == "alu"
     assert r["peak"] == pytest.approx(152 * 128 * 2000.0e6 / 1e12)
-    assert r["achieved"] == pytest.approx(1.0e11 * (64 + 16 + 12) / 1e12)
+    assert r["achieved"] == pytest.approx(2.0 * n * n * 64 / 0.02 / 1e12)
 
 
 def test_stale_traffic_is_not_reported():
@@ -58,10 +73,6 @@ def test_precision_constants_match_header():
 
 
 def test_bench_default_is_split_f16():
-    sys_argv = sys.argv
-    try:
-        sys.argv = ["bench.py"]
-        args = bench.parse()
-    finally:
-        sys.argv = sys_argv
+    args = bench.parse([])
     assert args.precision == "split_f16" and args.warmup >= 3 and args.gpus == 1
+    assert args.stop == "true" and args.workload == "gp1m"

@@ -1,7 +1,8 @@
-"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+"""CUDA path vs the FP64 oracle, through the C ABI.
 
 Tolerances (relative, max over columns of the 2-norm error unless stated):
-K-hat V 1e-5 (FP32 modes); solve true residual 1e-4; predictive mean 1e-4;
+K-hat V 1e-5 (FP32 modes), and every entry within 2e-5 of the sum
+sum_b |K-hat_ab| |V_bc| that forms it (tests/_parity.py); solve true residual 1e-4; predictive mean 1e-4;
 log-det 1e-3 against the same-probe target; gradient 1e-3 of the largest
 component against the same-probe gradient; pivots identical where the
 oracle's residual-diagonal gap exceeds 1e-9 s.
@@ -17,6 +18,9 @@ pytestmark = pytest.mark.gpu
 
 from oracle import gp_oracle as go  # noqa: E402
 from synth import make_workload  # noqa: E402
+from _parity import check_kmv, khat_ref, kcross_ref  # noqa: E402
+
+FORM = "fp32"
 
 
 @pytest.fixture(scope="module")
@@ -58,8 +62,8 @@ def test_kmatmul_gp2k(gp, ctx, w2k, precision):
     V = rng.standard_normal((16, w.N)).astype(np.float32)
     out = gp.gp_kmatmul(ctx, torch.from_numpy(w.X).cuda(), _theta(gp, w),
                         torch.from_numpy(V).cuda(), gp.PRECISIONS[precision])
-    ref = go.khat_matmul(w.X, V.T.astype(np.float64), w.lengthscale, 1.0, w.sigma2)
-    assert _relerr(out.cpu().numpy().T, ref) <= 1e-5
+    ref, aref = khat_ref(w.X, V.T, w.lengthscale, 1.0, w.sigma2)
+    check_kmv(out.cpu().numpy().T, ref, aref, 1e-5, precision)
 
 
 @pytest.mark.parametrize("N,d,t", [(1, 1, 1), (7, 3, 2), (129, 5, 3), (257, 33, 17),
@@ -71,8 +75,8 @@ def test_kmatmul_ragged(gp, ctx, N, d, t):
     V = rng.standard_normal((t, N)).astype(np.float32)
     th = gp.Theta(ell, 0.7, 1e-3)
     out = gp.gp_kmatmul(ctx, torch.from_numpy(X).cuda(), th, torch.from_numpy(V).cuda())
-    ref = go.khat_matmul(X, V.T.astype(np.float64), ell, 0.7, 1e-3)
-    assert _relerr(out.cpu().numpy().T, ref) <= 1e-5
+    ref, aref = khat_ref(X, V.T, ell, 0.7, 1e-3)
+    check_kmv(out.cpu().numpy().T, ref, aref, 1e-5, FORM)
 
 
 def test_kmatmul_single_point_is_exact(gp, ctx):
@@ -88,8 +92,8 @@ def test_kcross_matmul(gp, ctx, w2k):
     V = rng.standard_normal((3, w.N)).astype(np.float32)
     out = gp.gp_kcross_matmul(ctx, torch.from_numpy(w.Xtest).cuda(), torch.from_numpy(w.X).cuda(),
                               _theta(gp, w), torch.from_numpy(V).cuda())
-    ref = go.kcross_matmul(w.Xtest, w.X, V.T.astype(np.float64), w.lengthscale, 1.0)
-    assert _relerr(out.cpu().numpy().T, ref) <= 1e-5
+    ref, aref = kcross_ref(w.Xtest, w.X, V.T, w.lengthscale, 1.0)
+    check_kmv(out.cpu().numpy().T, ref, aref, 1e-5, FORM)
 
 
 @pytest.mark.parametrize("name,t,nrows", [("gp64k", 32, 256), ("gp1m", 16, 48)])
@@ -102,8 +106,8 @@ def test_kmatmul_full_size_sampled_rows(gp, ctx, name, t, nrows):
     out = gp.gp_kmatmul(ctx, torch.from_numpy(w.X).cuda(), _theta(gp, w),
                         torch.from_numpy(V).cuda()).cpu().numpy().T
     rows = np.sort(rng.choice(w.N, size=nrows, replace=False))
-    ref = go.khat_matmul_rows(w.X, V.T.astype(np.float64), w.lengthscale, 1.0, w.sigma2, rows)
-    assert _relerr(out[rows], ref) <= 1e-5
+    ref, aref = khat_ref(w.X, V.T, w.lengthscale, 1.0, w.sigma2, rows)
+    check_kmv(out[rows], ref, aref, 1e-5, FORM)
 
 
 # ------------------------------------------------------- pivoted Cholesky ----
@@ -153,7 +157,14 @@ def test_mbcg_solves_to_tolerance(gp, ctx, w2k):
 
 def test_mbcg_iterations_follow_the_oracle(gp, ctx):
     """Near-duplicate rows (sigma^2 = 1e-4): the GPU's FP32 PCG takes about
-    as many steps as the oracle's FP64 PCG, and its y column meets 1e-4."""
+    as many steps as the oracle's FP64 PCG.  Its true residual is gated at
+    2e-4, the attainable accuracy of FP32 storage on this problem: pairs at
+    distance ~1e-3 make K-hat ill-conditioned, and the FP32 rounding of the
+    iterate and of K's entries leaves the FP64 residual at ~1.8e-4 whatever
+    the recurrence reaches (a true-residual check measured with an FP32
+    product reads below 0.8e-4 there, itself limited by the same rounding).
+    The 1e-4 gate holds on the clustered workloads (test_gpu_tc.py,
+    test_gpu_f16.py)."""
     w = make_workload("gp64k", N=4096)
     X = torch.from_numpy(w.X).cuda()
     th = _theta(gp, w)
@@ -168,7 +179,7 @@ def test_mbcg_iterations_follow_the_oracle(gp, ctx):
     assert abs(int(r["iters"][0]) - int(ref["iters"][0])) <= 0.25 * ref["iters"][0] + 5
     Om = r["Omega"].cpu().numpy().T.astype(np.float64)
     res = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
-    assert res.max() <= 2e-4
+    assert res.max() <= 2e-4, res
 
 
 def test_mbcg_unpreconditioned_and_zero_column(gp, ctx):

@@ -63,7 +63,9 @@ def test_residual_diagonal_matches_oracle(gp, ctx):
 
 def test_mbcg_resid_solves_and_follows_oracle(gp, ctx):
     """Near-duplicate rows: the corrected form converges, with about the
-    oracle's number of steps."""
+    oracle's number of steps; its true residual is gated at the FP32
+    attainable accuracy of this ill-conditioned problem, 2e-4 (see
+    test_gpu_parity.py::test_mbcg_iterations_follow_the_oracle)."""
     w = make_workload("gp64k", N=4096)
     X = torch.from_numpy(w.X).cuda()
     th = _theta(gp, w)
@@ -82,7 +84,7 @@ def test_mbcg_resid_solves_and_follows_oracle(gp, ctx):
     assert abs(int(r["iters"][0]) - int(ref["iters"][0])) <= 0.4 * ref["iters"][0] + 5
     Om = r["Omega"].cpu().numpy().T.astype(np.float64)
     resid = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
-    assert resid.max() <= 2e-4
+    assert resid.max() <= 2e-4, resid
 
 
 @pytest.mark.parametrize("prec", ["fp32", "split_tf32"])

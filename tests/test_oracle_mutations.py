@@ -93,7 +93,16 @@ def _mutants():
         mean, var = orig_pred(X, y, Xp, ell, s, sig2, observation_noise)
         return mean, var - s
 
+    orig_psum = go.predict_sum
+
+    def psum_no_cross(X, y, Xp, ell, s, sig2):
+        # the variance of the sum taken as the sum of the pointwise variances
+        mean, _ = orig_psum(X, y, Xp, ell, s, sig2)
+        _, var = orig_pred(X, y, Xp, ell, s, sig2)
+        return mean, float(np.sum(var))
+
     return [
+        ("predict_sum", psum_no_cross, pins_love.test_predict_sum_is_the_sum_of_the_joint_posterior),
         ("matern52_of_r2", _matern_wrong_quadratic, pins_kernel.test_matern52_equals_bessel_family),
         ("khat_matmul", khat_no_noise, pins_kernel.test_khat_products_vs_brute_force),
         ("true_relative_residual", trr_no_noise, pins_kernel.test_true_relative_residual_vs_brute_force),

@@ -1,4 +1,5 @@
-"""gp_kmatmul_noalloc against gp_kmatmul, through the C ABI (GPU).
+"""gp_kmatmul_noalloc against the FP64 oracle and against gp_kmatmul,
+through the C ABI (GPU).
 
 gp_kmatmul_noalloc serves callers that may not allocate device memory (a
 process whose memory belongs to another framework's pool, a real-time loop
@@ -27,6 +28,7 @@ def test_noalloc_matches_kmatmul_twice_in_a_row():
     import paper_2109_09817_gb300 as gp
     from paper_2109_09817_gb300 import _lib
     from synth import make_workload
+    from _parity import check_kmv, khat_ref
 
     lib = _lib.load()
     ctx = gp.Context(0)
@@ -37,6 +39,8 @@ def test_noalloc_matches_kmatmul_twice_in_a_row():
         V = torch.randn(t, w.N, device="cuda", generator=torch.Generator("cuda").manual_seed(t))
         theta = gp.Theta(w.lengthscale, 0.9, 1e-3)
         ref = gp.gp_kmatmul(ctx, X, theta, V).cpu().numpy()
+        Vh = V.cpu().numpy().T.astype(np.float64)
+        oref, aref = khat_ref(w.X, Vh, w.lengthscale, 0.9, 1e-3)
         out = torch.full_like(V, float("nan"))
         th, keep = theta.as_c()
         rc = lib.gp_kmatmul_noalloc(ctypes.c_void_p(X.data_ptr()), w.N, w.d, ctypes.byref(th),
@@ -46,6 +50,9 @@ def test_noalloc_matches_kmatmul_twice_in_a_row():
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
+        # the oracle's FP64 product: the FP32 form's tolerance, column by
+        # column and entry by entry
+        check_kmv(got.T, oref, aref, 1e-5, "fp32")
         assert _relerr(got, ref) <= 1e-5
     # sizes beyond the fixed scratch are rejected before any work
     big = torch.zeros((70000, 4), device="cuda")
