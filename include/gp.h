@@ -75,6 +75,15 @@ enum {
   GP_TF32 = 3             /* tcgen05 kind::tf32, single-pass operands       */
 };
 
+/* GP_HOST, OR-ed into the `precision` argument of gp_kmatmul,
+ * gp_kcross_matmul and gp_logml_and_grad: their feature, vector and output
+ * arrays (X, Xp, V, out, y) are HOST memory.  The library copies the inputs
+ * into its device workspace on the context's stream (pinned memory copies
+ * asynchronously, pageable memory through the runtime's staging), runs the
+ * device path and copies out back; such a call synchronises.  The other
+ * arguments keep their meaning. */
+#define GP_HOST 0x100
+
 /* preconditioner forms (P = L L^T + D, L from the rank-k pivoted Cholesky) */
 enum {
   GP_PC_SIGMA = 0,  /* D = sigma^2 I: the form of Sec. 3.2                   */
@@ -324,6 +333,42 @@ GP_API int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
 GP_API int gp_kmatmul_noalloc(const float* X, int64_t N, int d,
                               const gp_theta* theta, const float* V, int t,
                               float* out, void* stream);
+
+/* ---- hyperparameter optimisation (Sec. 4, computational details) ---------
+ * gp_subset_indices: M distinct row indices of 0..N-1 drawn by a seeded
+ * partial Fisher-Yates shuffle (SplitMix64 stream from `seed`), sorted, into
+ * idx (HOST, M int64).  Runs on the host; GP_EINVAL for M > N or M < 1.
+ *
+ * gp_hyperopt: the paper optimises the hyperparameters on a random subset of
+ * the training data and does not name the optimiser; here `steps` steps of
+ * Adam (beta1 0.9, beta2 0.999, step `lr`) on log theta ascend the log
+ * marginal likelihood of Eq. (ll) on the `subset` rows chosen by
+ * gp_subset_indices(N, subset, seed), with the value and gradient of
+ * gp_logml_and_grad (n_probes trace probes from one fixed seed, so the
+ * objective is the same function of theta at every step; rank-k
+ * preconditioner of form `precond`, tol, max_iter, precision as there; a
+ * solve that reaches max_iter is used as it stands).  X: N x d, y: N
+ * (device).  lengthscale (d), outputscale, sigma2: HOST, the starting point
+ * on entry, the optimised values on return.  logml_hist (HOST, steps + 1,
+ * nullable): the objective at each visited theta, the last one at the
+ * returned theta; grad_out (HOST, d + 2, nullable): the gradient there.
+ * Synchronises.
+ *
+ * gp_train: gp_hyperopt, then gp_model_fit on all N rows with sigma^2 +
+ * sigma2_add (Sec. 4 adds sigma^2_add to the optimised noise before the
+ * full fit; block = 1, GP_STOP_RECURRENCE); the hyperparameters returned
+ * are the optimised ones, without sigma2_add. */
+GP_API int gp_subset_indices(int64_t N, int64_t M, uint64_t seed, int64_t* idx);
+GP_API int gp_hyperopt(gp_ctx* ctx, const float* X, int64_t N, int d, const float* y,
+                       int64_t subset, uint64_t seed, int steps, double lr, int n_probes,
+                       int k, int precond, double tol, int max_iter, int precision,
+                       double* lengthscale, double* outputscale, double* sigma2,
+                       double* logml_hist, double* grad_out);
+GP_API int gp_train(gp_ctx* ctx, const float* X, int64_t N, int d, const float* y,
+                    int64_t subset, uint64_t seed, int steps, double lr, int n_probes, int k,
+                    int precond, double tol, int max_iter, int precision, double sigma2_add,
+                    double* lengthscale, double* outputscale, double* sigma2,
+                    double* logml_hist, gp_model** out);
 
 /* ---- trained model and prediction (Eq. pred) ------------------------------
  * gp_model_fit keeps, on the device, the prepared features, a = K-hat^{-1} y,

@@ -444,20 +444,19 @@ def dkhat_dtheta(X, lengthscale, s):
     """Dense dK-hat/dtheta for theta = (l_1..l_d, s, sigma^2).
 
     dk/dl_j = s (5/3) (1 + sqrt5 r) exp(-sqrt5 r) (x_j - x'_j)^2 / l_j^3,
-    dk/ds = k / s, dK-hat/dsigma^2 = I.
+    dk/ds = k / s, dK-hat/dsigma^2 = I.  Yields the d + 2 matrices one at a
+    time, so that only one of them is held at once.
     """
     X = np.asarray(X, F64)
     ell = np.asarray(lengthscale, F64)
     r2 = sqdist(X, X, ell)
     r = np.sqrt(r2)
     g = s * (5.0 / 3.0) * (1.0 + SQRT5 * r) * np.exp(-SQRT5 * r)
-    mats = []
     for j in range(X.shape[1]):
         dj = (X[:, j:j + 1] - X[None, :, j]) ** 2 / ell[j] ** 3
-        mats.append(g * dj)
-    mats.append(matern52_of_r2(r2, s) / s)
-    mats.append(np.eye(X.shape[0]))
-    return mats
+        yield g * dj
+    yield matern52_of_r2(r2, s) / s
+    yield np.eye(X.shape[0])
 
 
 def exact_grad(X, y, lengthscale, s, sigma2):

@@ -16,13 +16,14 @@ GP_VAR_CACHE_MAX_RANK = 128
 GP_PC_SIGMA, GP_PC_RESID = 0, 1
 GP_STOP_RECURRENCE, GP_STOP_TRUE = 0, 1
 GP_OPT_SYMMETRIC_KMV = 1
+GP_HOST = 0x100
 
 # Every symbol include/gp.h declares.
 EXPORTS = (
     "gp_create", "gp_destroy", "gp_set_stream", "gp_sync", "gp_last_error",
     "gp_launch_count", "gp_set_option", "gp_profile", "gp_profile_read", "gp_kmatmul", "gp_kcross_matmul", "gp_pivchol", "gp_mbcg",
     "gp_mbcg_refine", "gp_bcg", "gp_logml_and_grad", "gp_model_fit", "gp_model_free", "gp_predict",
-    "gp_model_variance_cache", "gp_predict_sum",
+    "gp_model_variance_cache", "gp_predict_sum", "gp_subset_indices", "gp_hyperopt", "gp_train",
     "gp_kmatmul_noalloc", "gp_server_create", "gp_server_add_model", "gp_server_predict", "gp_server_molecule",
     "gp_server_solve", "gp_server_wait", "gp_server_stats", "gp_server_last_error",
     "gp_server_destroy",
@@ -92,6 +93,11 @@ def load(path: str = LIB_PATH):
         "gp_predict": (c_int, [vp, vp, vp, i64, vp, vp, c_int]),
         "gp_model_variance_cache": (c_int, [vp, vp, vp, c_int, ip]),
         "gp_predict_sum": (c_int, [vp, vp, vp, i64, dp, dp, c_int]),
+        "gp_subset_indices": (c_int, [i64, i64, ctypes.c_uint64, ctypes.POINTER(i64)]),
+        "gp_hyperopt": (c_int, [vp, vp, i64, c_int, vp, i64, ctypes.c_uint64, c_int, c_dbl, c_int, c_int,
+                                c_int, c_dbl, c_int, c_int, dp, dp, dp, dp, dp]),
+        "gp_train": (c_int, [vp, vp, i64, c_int, vp, i64, ctypes.c_uint64, c_int, c_dbl, c_int, c_int,
+                             c_int, c_dbl, c_int, c_int, c_dbl, dp, dp, dp, dp, ctypes.POINTER(vp)]),
         "gp_kmatmul_noalloc": (c_int, [vp, i64, c_int, th, vp, c_int, vp, vp]),
         "gp_server_create": (c_int, [ctypes.POINTER(vp), c_int, i64, c_dbl]),
         "gp_server_add_model": (c_int, [vp, vp, i64, c_int, th, vp, c_int, c_int, c_dbl, c_int,

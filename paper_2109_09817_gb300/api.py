@@ -129,6 +129,32 @@ def gp_kmatmul(ctx: Context, X: torch.Tensor, theta: Theta, V: torch.Tensor,
     return out
 
 
+def _host(a, name):
+    """A host array argument (numpy, or a CPU torch tensor, e.g. pinned):
+    float32, C-contiguous; returns (pointer, keep-alive)."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 host tensor")
+        return ctypes.c_void_p(a.data_ptr()), a
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a.ctypes.data_as(ctypes.c_void_p), a
+
+
+def gp_kmatmul_host(ctx: Context, X, theta: Theta, V, precision: int = GP_FP32_PLAIN):
+    """gp_kmatmul with GP_HOST: X (N, d) and V (t, N) in host memory; returns
+    the (t, N) result as a numpy array (the call synchronises)."""
+    xp, xk = _host(X, "X")
+    N, d = xk.shape
+    V = V.reshape(1, -1) if V.ndim == 1 else V
+    vp, vk = _host(V, "V")
+    t = vk.shape[0]
+    out = np.empty((t, N), dtype=np.float32)
+    th, keep = theta.as_c()
+    ctx.check(ctx.lib.gp_kmatmul(ctx.h, xp, N, d, ctypes.byref(th), vp, t,
+                                 out.ctypes.data_as(ctypes.c_void_p), precision | _lib.GP_HOST))
+    return out
+
+
 def gp_kcross_matmul(ctx: Context, Xp: torch.Tensor, X: torch.Tensor, theta: Theta,
                      V: torch.Tensor, precision: int = GP_FP32_PLAIN):
     """K(X', X) V; V is (t, N), the result (t, M)."""
@@ -273,6 +299,30 @@ def gp_logml_and_grad(ctx: Context, X: torch.Tensor, theta: Theta, y: torch.Tens
                 grad=np.array(grad[:]) if want_grad else None, stats=stats.as_dict(), rc=rc)
 
 
+def gp_logml_and_grad_host(ctx: Context, X, theta: Theta, y, n_probes: int = 15, seed: int = 0,
+                           k: int = 32, tol: float = 1e-6, max_iter: int = 1000,
+                           precision: int = GP_FP32_PLAIN, want_grad: bool = True,
+                           allow_notconv: bool = False, precond: int = GP_PC_SIGMA,
+                           stop: int = GP_STOP_RECURRENCE):
+    """gp_logml_and_grad with GP_HOST: X (N, d) and y (N,) in host memory."""
+    xp, xk = _host(X, "X")
+    yp, yk = _host(y, "y")
+    N, d = xk.shape
+    logml = ctypes.c_double()
+    logdet = ctypes.c_double()
+    se = ctypes.c_double()
+    grad = (ctypes.c_double * (d + 2))()
+    stats = _lib.GpStats()
+    th, keep = theta.as_c()
+    allow = (GP_ENOTCONV,) if allow_notconv else ()
+    rc = ctx.check(ctx.lib.gp_logml_and_grad(
+        ctx.h, xp, N, d, ctypes.byref(th), yp, n_probes, ctypes.c_uint64(seed), k, precond, tol,
+        max_iter, stop, precision | _lib.GP_HOST, ctypes.byref(logml), ctypes.byref(logdet),
+        grad if want_grad else None, ctypes.byref(se), ctypes.byref(stats)), allow=allow)
+    return dict(logml=logml.value, logdet=logdet.value, logdet_stderr=se.value,
+                grad=np.array(grad[:]) if want_grad else None, stats=stats.as_dict(), rc=rc)
+
+
 class Model:
     """A fitted model resident on the device (gp_model_fit / gp_predict)."""
 
@@ -292,6 +342,12 @@ class Model:
                                        max_iter, stop, precision, ctypes.byref(h), ctypes.byref(stats)))
         self.h = h
         self.stats = stats.as_dict()
+
+    @classmethod
+    def _from_handle(cls, ctx: Context, h, N: int, d: int):
+        m = cls.__new__(cls)
+        m.ctx, m.h, m.N, m.d, m.stats = ctx, h, N, d, None
+        return m
 
     def free(self):
         if getattr(self, "h", None):
@@ -342,6 +398,64 @@ def gp_predict_sum(ctx: Context, model: Model, Xp: torch.Tensor, var_mode: int =
     ctx.check(ctx.lib.gp_predict_sum(ctx.h, model.h, _p(Xp), Xp.shape[0], ctypes.byref(ms),
                                      ctypes.byref(vs) if var_mode else None, var_mode))
     return ms.value, (vs.value if var_mode else None)
+
+
+def gp_subset_indices(N: int, M: int, seed: int) -> np.ndarray:
+    """M distinct sorted row indices of 0..N-1 (seeded partial shuffle)."""
+    lib = _lib.load()
+    idx = np.empty(M, dtype=np.int64)
+    rc = lib.gp_subset_indices(N, M, ctypes.c_uint64(seed),
+                               idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc != GP_OK:
+        raise GPError(rc, "gp_subset_indices: bad arguments")
+    return idx
+
+
+def _hyper_args(theta: Theta, d: int):
+    ell = np.ascontiguousarray(theta.lengthscale, dtype=np.float64).copy()
+    if ell.shape != (d,):
+        raise ValueError(f"lengthscale must have {d} entries")
+    return ell, ctypes.c_double(theta.outputscale), ctypes.c_double(theta.sigma2)
+
+
+def gp_hyperopt(ctx: Context, X: torch.Tensor, y: torch.Tensor, theta0: Theta, subset: int,
+                seed: int = 0, steps: int = 10, lr: float = 0.05, n_probes: int = 15, k: int = 32,
+                precond: int = GP_PC_RESID, tol: float = 1e-4, max_iter: int = 1000,
+                precision: int = GP_FP32_SPLIT_F16):
+    """Adam on log theta over a seeded random subset (Sec. 4); returns
+    (theta, logml history of steps + 1 values, gradient at theta)."""
+    _dev(ctx, X, torch.float32, "X")
+    _dev(ctx, y, torch.float32, "y")
+    N, d = X.shape
+    ell, s, s2 = _hyper_args(theta0, d)
+    hist = np.zeros(steps + 1)
+    grad = np.zeros(d + 2)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ctx.check(ctx.lib.gp_hyperopt(ctx.h, _p(X), N, d, _p(y), subset, ctypes.c_uint64(seed), steps, lr,
+                                  n_probes, k, precond, tol, max_iter, precision, ell.ctypes.data_as(dp),
+                                  ctypes.byref(s), ctypes.byref(s2), hist.ctypes.data_as(dp),
+                                  grad.ctypes.data_as(dp)))
+    return Theta(ell, s.value, s2.value), hist, grad
+
+
+def gp_train(ctx: Context, X: torch.Tensor, y: torch.Tensor, theta0: Theta, subset: int,
+             seed: int = 0, steps: int = 10, lr: float = 0.05, n_probes: int = 15, k: int = 32,
+             precond: int = GP_PC_RESID, tol: float = 1e-4, max_iter: int = 1000,
+             precision: int = GP_FP32_SPLIT_F16, sigma2_add: float = 1e-5):
+    """gp_hyperopt, then the full fit with sigma^2 + sigma2_add; returns
+    (Model, optimised theta, logml history)."""
+    _dev(ctx, X, torch.float32, "X")
+    _dev(ctx, y, torch.float32, "y")
+    N, d = X.shape
+    ell, s, s2 = _hyper_args(theta0, d)
+    hist = np.zeros(steps + 1)
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    ctx.check(ctx.lib.gp_train(ctx.h, _p(X), N, d, _p(y), subset, ctypes.c_uint64(seed), steps, lr,
+                               n_probes, k, precond, tol, max_iter, precision, sigma2_add,
+                               ell.ctypes.data_as(dp), ctypes.byref(s), ctypes.byref(s2),
+                               hist.ctypes.data_as(dp), ctypes.byref(h)))
+    return Model._from_handle(ctx, h, N, d), Theta(ell, s.value, s2.value), hist
 
 
 class Server:

@@ -126,6 +126,24 @@ int prep_train(gp_ctx* ctx, const float* X, int64_t N, int d,
 bool valid_precision(int p) { return p >= GP_FP32_PLAIN && p <= GP_TF32; }
 bool valid_stop(int r) { return r == GP_STOP_RECURRENCE || r == GP_STOP_TRUE; }
 
+// host array -> device workspace slot (asynchronous on the context stream
+// for pinned memory; the runtime stages pageable memory itself)
+const float* stage_in(gp_ctx* ctx, int slot, const float* src, size_t bytes) {
+  float* dst = static_cast<float*>(ws_get(ctx, slot, bytes));
+  if (!dst) return nullptr;
+  if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return dst;
+}
+
+int stage_out(gp_ctx* ctx, float* dst, const float* src, size_t bytes) {
+  GP_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
+}
+
 __global__ void fill_one_kernel(float* __restrict__ v, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = 1.f;
@@ -254,6 +272,17 @@ int gp_profile_read(gp_ctx* ctx, int64_t* products, double* ms, double* flops,
 int gp_kmatmul(gp_ctx* ctx, const float* X, int64_t N, int d,
                const gp_theta* theta, const float* V, int t, float* out,
                int precision) {
+  if (ctx && (precision & GP_HOST)) {
+    // host arrays: stage X and V on the device, run, copy out back
+    GP_TRY(check_common(ctx, X, N, d, theta));
+    if (!V || !out || t < 1 || t > kMaxT) return set_err(ctx, GP_EINVAL, "gp_kmatmul: bad V/out/t");
+    const float* Xd = stage_in(ctx, WS_HS_X, X, sizeof(float) * (size_t)N * d);
+    const float* Vd = stage_in(ctx, WS_HS_V, V, sizeof(float) * (size_t)N * t);
+    float* Od = ws<float>(ctx, WS_HS_O, (size_t)N * t);
+    if (!Xd || !Vd || !Od) return set_err(ctx, GP_ENOMEM, "workspace (host arrays)");
+    GP_TRY(gp_kmatmul(ctx, Xd, N, d, theta, Vd, t, Od, precision & ~GP_HOST));
+    return stage_out(ctx, out, Od, sizeof(float) * (size_t)N * t);
+  }
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!V || !out || t < 1 || t > kMaxT || !valid_precision(precision))
     return set_err(ctx, GP_EINVAL, "gp_kmatmul: bad V/out/t/precision");
@@ -266,6 +295,18 @@ int gp_kmatmul(gp_ctx* ctx, const float* X, int64_t N, int d,
 int gp_kcross_matmul(gp_ctx* ctx, const float* Xp, int64_t M, const float* X,
                      int64_t N, int d, const gp_theta* theta, const float* V,
                      int t, float* out, int precision) {
+  if (ctx && (precision & GP_HOST)) {
+    GP_TRY(check_common(ctx, X, N, d, theta));
+    if (!Xp || M <= 0 || !V || !out || t < 1 || t > kMaxT)
+      return set_err(ctx, GP_EINVAL, "gp_kcross_matmul: bad arguments");
+    const float* Xd = stage_in(ctx, WS_HS_X, X, sizeof(float) * (size_t)N * d);
+    const float* Xpd = stage_in(ctx, WS_HS_XP, Xp, sizeof(float) * (size_t)M * d);
+    const float* Vd = stage_in(ctx, WS_HS_V, V, sizeof(float) * (size_t)N * t);
+    float* Od = ws<float>(ctx, WS_HS_O, (size_t)M * t);
+    if (!Xd || !Xpd || !Vd || !Od) return set_err(ctx, GP_ENOMEM, "workspace (host arrays)");
+    GP_TRY(gp_kcross_matmul(ctx, Xpd, M, Xd, N, d, theta, Vd, t, Od, precision & ~GP_HOST));
+    return stage_out(ctx, out, Od, sizeof(float) * (size_t)M * t);
+  }
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!Xp || M <= 0 || !V || !out || t < 1 || t > kMaxT || !valid_precision(precision))
     return set_err(ctx, GP_EINVAL, "gp_kcross_matmul: bad arguments");
@@ -487,6 +528,15 @@ int gp_logml_and_grad(gp_ctx* ctx, const float* X, int64_t N, int d,
                       uint64_t seed, int k, int precond, double tol, int max_iter,
                       int stop_rule, int precision, double* logml, double* logdet,
                       double* grad, double* logdet_stderr, gp_stats* stats) {
+  if (ctx && (precision & GP_HOST)) {
+    GP_TRY(check_common(ctx, X, N, d, theta));
+    if (!y) return set_err(ctx, GP_EINVAL, "gp_logml_and_grad: null y");
+    const float* Xd = stage_in(ctx, WS_HS_X, X, sizeof(float) * (size_t)N * d);
+    const float* yd = stage_in(ctx, WS_HS_V, y, sizeof(float) * (size_t)N);
+    if (!Xd || !yd) return set_err(ctx, GP_ENOMEM, "workspace (host arrays)");
+    return gp_logml_and_grad(ctx, Xd, N, d, theta, yd, n_probes, seed, k, precond, tol, max_iter, stop_rule,
+                             precision & ~GP_HOST, logml, logdet, grad, logdet_stderr, stats);
+  }
   GP_TRY(check_common(ctx, X, N, d, theta));
   if (!y || n_probes < 1 || n_probes > 255 || k < 0 || k > N || max_iter < 1 ||
       !(tol >= 0.0) || !logml || !logdet || !valid_precision(precision) || !valid_stop(stop_rule) ||

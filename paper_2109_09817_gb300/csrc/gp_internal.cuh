@@ -54,6 +54,8 @@ enum WsSlot {
   WS_BC_C, WS_BC_P, WS_BC_W, WS_BC_S, WS_BC_R, WS_BC_RH, WS_BC_D, WS_BC_D2, WS_BC_DT,
   WS_BC_WK, WS_BC_Q, WS_BC_OM, WS_BC_M, WS_BC_DH, WS_PC_DH64, WS_CG_W64,
   WS_LV_W, WS_LV_P, WS_LV_T, WS_LV_K, WS_LV_M, WS_LV_C,
+  WS_HO_IDX, WS_HO_X, WS_HO_Y,
+  WS_HS_X, WS_HS_XP, WS_HS_V, WS_HS_O,
   WS_COUNT
 };
 

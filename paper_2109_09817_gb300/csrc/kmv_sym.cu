@@ -22,13 +22,15 @@
 //         written to TMEM over S (A of the first contraction) and to a
 //         128B-swizzled SMEM tile K[a][b] (A of the second, read MN-major)
 //   MMA2  O_I += K_hi [V_hi; V_lo]_J + K_lo V_hi,J  (M = 128, A from TMEM)
-//         D_J  = K_hi^T [V_hi; V_lo]_I + K_lo^T V_hi,I (M = 64, A = K^T from
-//         SMEM, MN-major; V_I loaded once per segment)
+//   MMAT  for a pair of consecutive column tiles J, J + 1 (128 columns b):
+//         D = K_hi^T [V_hi; V_lo]_I + K_lo^T V_hi,I (M = 128, A = K^T of both
+//         tiles read MN-major from their adjacent SMEM tiles; V_I loaded
+//         once per segment)
 //   epi   O_I drained into per-thread compensated sums every OGROUP tiles of
-//         a group; D_J drained per tile and added into out with atomics
-// Warp roles: 0 TMA producer, 1 MMA1 issuer, 2 TMEM allocator, 3 MMA2
-// issuer, 4..19 two epilogue groups of 8 warps (group g takes tiles j with
-// j % 2 == g).  Every mbarrier wait is bounded; a timeout records
+//         a group; each pair's D drained once and added into out with atomics
+// Warp roles: 0 TMA producer, 1 MMA1 issuer, 2 TMEM allocator and MMAT
+// issuer, 3 MMA2 issuer, 4..19 two epilogue groups of 8 warps (group g takes
+// tiles j with j % 2 == g, and drains the pairs p with p % 2 == g).  Every mbarrier wait is bounded; a timeout records
 // GP_ETIMEOUT in the status word and every role leaves its loop.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -52,11 +54,13 @@ constexpr int DPH = kHalfCols;  // FP16 features per row: one 128-byte box
 
 template <int T>
 struct SymLayout {
-  static constexpr int NSB = 3;                  // S/K buffers (TMEM and SMEM)
-  static constexpr int XS = 4;                   // X~_J ring slots
+  // S/K buffers (TMEM and SMEM), an even number: the tiles of a pair sit in
+  // adjacent buffers, so that one MN-major descriptor spans both
+  static constexpr int NSB = T <= 16 ? 4 : 2;
+  static constexpr int XS = T <= 16 ? 3 : 4;     // X~_J ring slots
   static constexpr int VS = 4;                   // V_J ring slots
   static constexpr int OB = T <= 16 ? 2 : 1;     // O_I accumulators per epilogue group
-  static constexpr int DB = T <= 16 ? 2 : 1;     // D_J accumulators per epilogue group
+  static constexpr int DP = 2;                   // pair D accumulators (M = 128, 2T columns)
   static constexpr int XJ_BOX = BN * 128;        // 64 rows x 128 B
   static constexpr int V_BOX = T * 128;          // T vectors x 64 FP16 columns
   static constexpr int KT = BM * 128;            // one K part: 128 rows a x 64 columns b, FP16
@@ -70,7 +74,7 @@ struct SymLayout {
   static constexpr int V_SLOT = (V_NRM + 256 + 1023) / 1024 * 1024;
   static constexpr int V0 = X0 + XS * X_SLOT;
   static constexpr int BAR = V0 + VS * V_SLOT;
-  static constexpr int NBAR = 2 * XS + 2 * VS + 1 + 3 * NSB + 4 * OB + 4 * DB + 1;
+  static constexpr int NBAR = 2 * XS + 2 * VS + 1 + 3 * NSB + 4 * OB + 2 * DP + 1;
   static constexpr int TOTAL = BAR + NBAR * 8 + 16;
   static constexpr uint32_t TX_X = 2u * XJ_BOX;
   static constexpr uint32_t TX_V = 2u * V_BOX + 256u;
@@ -79,9 +83,10 @@ struct SymLayout {
   static constexpr uint32_t T_XA = 0;                      // X~_I: hi [0, 32), lo [32, 64)
   static constexpr uint32_t T_S = 64;                      // S/K buffers, 64 columns each
   static constexpr uint32_t T_O = T_S + NSB * 64;          // O_I [group][buffer] x 2T
-  static constexpr uint32_t T_D = T_O + 2 * OB * 2 * T;    // D_J [group][buffer] x 2T
+  static constexpr uint32_t T_D = T_O + 2 * OB * 2 * T;    // pair D [buffer] x 2T
   static constexpr uint32_t T_COLS = 512;
-  static_assert(T_D + 2 * DB * 2 * T <= T_COLS, "TMEM columns");
+  static_assert(T_D + DP * 2 * T <= T_COLS, "TMEM columns");
+  static_assert(NSB % 2 == 0, "pairs need adjacent buffers");
   static_assert(TOTAL + 2048 <= 232448, "shared memory");
 };
 
@@ -121,11 +126,12 @@ __device__ __forceinline__ bool segment_of(const SymParams& p, int blk, int* I, 
 
 // SMEM descriptor of an MN-major operand in the 128B-swizzled layout: rows
 // of 128 bytes are consecutive K indices, each holding 64 FP16 along M; 8
-// such rows form a 1024-byte atom, atoms follow each other along K (SBO).
-// M = 64 is one atom wide, so the leading offset is not used.
-__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(8192 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// such rows form a 1024-byte atom, atoms follow each other along K (SBO =
+// 1024 bytes); the second 64 elements of M (the pair's second tile) sit
+// `lbo` bytes on (the leading byte offset).
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 // A operand MN-major (bit 15 of the instruction descriptor)
 __host__ __device__ constexpr uint32_t idesc_f16_amn(int M, int N) { return idesc_f16(M, N) | (1u << 15); }
@@ -158,10 +164,11 @@ __device__ __forceinline__ void mma2_sym_steps(uint32_t d, uint32_t khi, uint64_
     mma2_sym_steps<Ly, KK + 1>(d, khi, dV, id2w, id2, acc0);
   }
 }
-// Second contraction: D[0, 2T) = K_hi^T [V_hi; V_lo]_I, D[0, T) += K_lo^T
-// V_hi,I, M = 64 (the columns b), K = the 128 rows a in k-steps of 16: A =
-// K^T read MN-major from the SMEM tile (16 rows a = 2048 bytes per k-step),
-// B = the V_I slot (64 rows a per 128-byte box, 32 bytes per k-step).
+// Second contraction of a pair: D[0, 2T) = K_hi^T [V_hi; V_lo]_I, D[0, T)
+// += K_lo^T V_hi,I, M = 128 (the 64 columns b of each tile), K = the 128 rows
+// a in k-steps of 16: A = K^T read MN-major from the two SMEM tiles (16 rows
+// a = 2048 bytes per k-step), B = the V_I slot (64 rows a per 128-byte box,
+// 32 bytes per k-step).
 template <class Ly, int KK>
 __device__ __forceinline__ void mmat_sym_steps(uint32_t d, uint64_t dKh, uint64_t dKl, uint64_t dVI, uint32_t idw,
                                                uint32_t id) {
@@ -185,7 +192,7 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
                const __grid_constant__ CUtensorMap map_v_hi, const __grid_constant__ CUtensorMap map_v_lo,
                const SymParams p) {
   using Ly = SymLayout<T>;
-  constexpr int NSB = Ly::NSB, XS = Ly::XS, VS = Ly::VS, OB = Ly::OB, DB = Ly::DB;
+  constexpr int NSB = Ly::NSB, XS = Ly::XS, VS = Ly::VS, OB = Ly::OB, DP = Ly::DP;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Ly::BAR);
@@ -196,14 +203,15 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
   uint64_t* bar_vi = bar_ve + VS;          // V_I loaded
   uint64_t* bar_s = bar_vi + 1;            // [NSB] S in buffer b ready
   uint64_t* bar_k = bar_s + NSB;           // [NSB] K of buffer b written (TMEM and SMEM)
-  uint64_t* bar_kf = bar_k + NSB;          // [NSB] ... read by both contractions
+  uint64_t* bar_kf = bar_k + NSB;          // [NSB] ... read by both contractions (2 arrivals)
   uint64_t* bar_of = bar_kf + NSB;         // [2 OB] O_I of group g, buffer u ready
   uint64_t* bar_oe = bar_of + 2 * OB;      // [2 OB] ... drained
-  uint64_t* bar_df = bar_oe + 2 * OB;      // [2 DB] D_J of group g, buffer v ready
-  uint64_t* bar_de = bar_df + 2 * DB;      // [2 DB] ... drained
-  uint64_t* bar_fin = bar_de + 2 * DB;     // both MMA issuers drained
+  uint64_t* bar_df = bar_oe + 2 * OB;      // [DP] pair D in buffer v ready
+  uint64_t* bar_de = bar_df + DP;          // [DP] ... drained
+  uint64_t* bar_fin = bar_de + DP;         // the three MMA issuers drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + Ly::NBAR);
   __shared__ int fail;
+  __shared__ float out_scale[T];           // s 2^-(e_c + 14) per output vector
 
   int I, jt0, jt1;
   if (!segment_of(p, blockIdx.x, &I, &jt0, &jt1)) return;
@@ -215,6 +223,7 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
   const int ntiles = jt1 - jt0;
   const int jt_off = 2 * I + 2;            // tiles from here on are off the diagonal block
 
+  if (threadIdx.x < T) out_scale[threadIdx.x] = threadIdx.x < p.t ? p.s * p.vsc[threadIdx.x] : 0.f;
   if (threadIdx.x == 0) {
     fail = 0;
     for (int i = 0; i < XS; ++i) {
@@ -229,17 +238,17 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
     for (int i = 0; i < NSB; ++i) {
       mbar_init(bar_s + i, 1);
       mbar_init(bar_k + i, GROUP_WARPS);
-      mbar_init(bar_kf + i, 1);
+      mbar_init(bar_kf + i, 2);
     }
     for (int i = 0; i < 2 * OB; ++i) {
       mbar_init(bar_of + i, 1);
       mbar_init(bar_oe + i, GROUP_WARPS);
     }
-    for (int i = 0; i < 2 * DB; ++i) {
+    for (int i = 0; i < DP; ++i) {
       mbar_init(bar_df + i, 1);
       mbar_init(bar_de + i, GROUP_WARPS);
     }
-    mbar_init(bar_fin, 2);
+    mbar_init(bar_fin, 3);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -327,21 +336,16 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
     mma_commit(bar_fin);
     mbar_wait_exit(bar_fin, 0);
   } else if (warp == 3 && lane == 0) {
-    // ------------------------------------------------------- MMA2 issuer --
+    // ------------------------------------------------ first contraction --
     // Tile j: S/K buffer b = j % NSB, group g = j & 1, the group's i-th tile
     // with i = j >> 1; O_I accumulates OGROUP of the group's tiles in buffer
-    // u = (i / OGROUP) % OB; D_J goes to buffer v = i % DB.  Diagonal-block
-    // tiles take the first contraction only, but commit D_J's barrier all
-    // the same so that every barrier's phase counts the group's tiles.
+    // u = (i / OGROUP) % OB.
     constexpr uint32_t ID2 = idesc_f16(BM, T), ID2W = idesc_f16(BM, 2 * T);
-    constexpr uint32_t IDT = idesc_f16_amn(64, T), IDTW = idesc_f16_amn(64, 2 * T);
     const uint64_t dV0 = sdesc(su32(smem + Ly::V0));
-    const uint64_t dVI = sdesc(su32(smem + Ly::VI0));
-    const uint64_t dK0 = sdesc_mn(su32(smem + Ly::K0));
-    bool ok = true, vi_ready = false;
+    bool ok = true;
     for (int j = 0; ok && j < ntiles; ++j) {
       const int b = j % NSB, vs = j % VS, g = j & 1, i = j >> 1;
-      const int og = i / OGROUP, u = og % OB, v = i % DB;
+      const int og = i / OGROUP, u = og % OB;
       const bool first = (i % OGROUP) == 0;
       const bool last = (i % OGROUP) == OGROUP - 1 || j + 2 >= ntiles;
       if (!(ok = mbar_wait(bar_k + b, (j / NSB) & 1, &fail))) break;
@@ -356,22 +360,46 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
       mma2_sym_steps<Ly, 0>(tbase + Ly::T_O + (g * OB + u) * 2 * T, tbase + Ly::T_S + b * 64, dV, ID2W, ID2,
                             first ? 0u : 1u);
       if (last) mma_commit(bar_of + g * OB + u);
-      if (i >= DB) {
-        if (!(ok = mbar_wait(bar_de + g * DB + v, ((i - DB) / DB) & 1, &fail))) break;
+      mma_commit(bar_ve + vs);
+      mma_commit(bar_kf + b);
+    }
+    mma_commit(bar_fin);
+    mbar_wait_exit(bar_fin, 0);
+  } else if (warp == 2 && lane == 0) {
+    // ----------------------------------------------- second contraction --
+    // Pair p = tiles 2p, 2p + 1 (the second may not exist at the end of a
+    // segment; its half of D is then not drained), in buffers b0 = 2p % NSB
+    // and b0 + 1, D in buffer v = p % DP.  The diagonal block is always a
+    // whole pair (the first of a row tile's first segment) and takes no
+    // second contraction, but commits the same barriers, so that every
+    // barrier's phase counts pairs and tiles.
+    constexpr uint32_t IDT = idesc_f16_amn(BM, T), IDTW = idesc_f16_amn(BM, 2 * T);
+    const uint64_t dVI = sdesc(su32(smem + Ly::VI0));
+    const uint64_t dK0 = sdesc_mn(su32(smem + Ly::K0), 2 * Ly::KT);
+    const int npairs = (ntiles + 1) / 2;
+    bool ok = true, vi_ready = false;
+    for (int pr = 0; ok && pr < npairs; ++pr) {
+      const int j0 = 2 * pr, b0 = j0 % NSB, v = pr % DP;
+      const bool two = j0 + 1 < ntiles;
+      if (!(ok = mbar_wait(bar_k + b0, (j0 / NSB) & 1, &fail))) break;
+      if (two && !(ok = mbar_wait(bar_k + b0 + 1, ((j0 + 1) / NSB) & 1, &fail))) break;
+      fence_after();
+      if (pr >= DP) {
+        if (!(ok = mbar_wait(bar_de + v, ((pr - DP) / DP) & 1, &fail))) break;
         fence_after();
       }
-      if (jt0 + j >= jt_off) {
+      if (jt0 + j0 >= jt_off) {
         if (!vi_ready) {
           if (!(ok = mbar_wait(bar_vi, 0, &fail))) break;
           fence_after();
           vi_ready = true;
         }
-        const uint64_t dKh = dK0 + (uint64_t)((b * 2 * Ly::KT) >> 4);
-        mmat_sym_steps<Ly, 0>(tbase + Ly::T_D + (g * DB + v) * 2 * T, dKh, dKh + (Ly::KT >> 4), dVI, IDTW, IDT);
+        const uint64_t dKh = dK0 + (uint64_t)((b0 * 2 * Ly::KT) >> 4);
+        mmat_sym_steps<Ly, 0>(tbase + Ly::T_D + v * 2 * T, dKh, dKh + (Ly::KT >> 4), dVI, IDTW, IDT);
       }
-      mma_commit(bar_df + g * DB + v);
-      mma_commit(bar_ve + vs);
-      mma_commit(bar_kf + b);
+      mma_commit(bar_df + v);
+      mma_commit(bar_kf + b0);
+      if (two) mma_commit(bar_kf + b0 + 1);
     }
     mma_commit(bar_fin);
     mbar_wait_exit(bar_fin, 0);
@@ -420,36 +448,38 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
       if (lane == 0) mbar_arrive(bar_oe + g * OB + u);
       return true;
     };
-    // D_J of the group's tile i: rows b of the M = 64 product sit in lanes
-    // 0..15 of each TMEM lane quarter (row 16 q + l in lane 32 q + l); warp
-    // half h adds outputs [h TH, +TH) of those rows into out
-    auto drain_d = [&](int i) -> bool {
-      const int j = 2 * i + g, v = i % DB;
-      if (!mbar_wait(bar_df + g * DB + v, (i / DB) & 1, &fail)) return false;
+    // The pair's D (M = 128): row r = 32 q + lane is column b = 64 (jt0 + 2p)
+    // + r of K (rows 64.. belong to the pair's second tile); warp half h adds
+    // outputs [h TH, +TH) of its rows into out
+    const int npairs = (ntiles + 1) / 2;
+    auto drain_d = [&](int pr) -> bool {
+      const int v = pr % DP;
+      if (!mbar_wait(bar_df + v, (pr / DP) & 1, &fail)) return false;
       fence_after();
-      if (jt0 + j >= jt_off) {
-        const uint32_t da = tbase + lane_off + Ly::T_D + (g * DB + v) * 2 * T + h * TH;
-        const int64_t bcol = (int64_t)(jt0 + j) * BN + q * 16 + lane;
+      if (jt0 + 2 * pr >= jt_off) {
+        const uint32_t da = tbase + lane_off + Ly::T_D + v * 2 * T + h * TH;
+        const int64_t bcol = (int64_t)(jt0 + 2 * pr) * BN + r;
+        const bool live = bcol < p.n && bcol < (int64_t)(jt0 + ntiles) * BN;
 #pragma unroll
         for (int c8 = 0; c8 < TH; c8 += 8) {
           uint32_t rr[8], rx[8];
           tmem_ld8(da + c8, rr);
           tmem_ld8(da + T + c8, rx);
           tmem_wait_ld();
-          if (lane < 16 && bcol < p.n) {
+          if (live) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               const int col = h * TH + c8 + c;
               if (col < p.t)
                 atomicAdd(p.out + (int64_t)col * p.ldo + bcol,
-                          p.s * p.vsc[col] * (__uint_as_float(rr[c]) + __uint_as_float(rx[c])));
+                          out_scale[col] * (__uint_as_float(rr[c]) + __uint_as_float(rx[c])));
             }
           }
         }
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar_de + g * DB + v);
+      if (lane == 0) mbar_arrive(bar_de + v);
       return true;
     };
     bool ok = true;
@@ -511,15 +541,18 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_k + b);
       if ((i % OGROUP) == 0 && i > 0 && !(ok = drain_o(i / OGROUP - 1))) break;
-      if (i > 0 && !(ok = drain_d(i - 1))) break;
+      // pair i - 1 (tiles 2i - 2, 2i - 1) is complete once both groups have
+      // passed it; the group of its parity drains it
+      if (i > 0 && ((i - 1) & 1) == g && !(ok = drain_d(i - 1))) break;
     }
     if (ok && my_tiles > 0) ok = drain_o((my_tiles - 1) / OGROUP);
-    if (ok && my_tiles > 0) ok = drain_d(my_tiles - 1);
+    for (int pr = max(0, my_tiles - 1); ok && pr < npairs; ++pr)
+      if ((pr & 1) == g) ok = drain_d(pr);
     if (ok && my_tiles > 0 && grow < p.n) {
 #pragma unroll
       for (int c = 0; c < TH; ++c) {
         const int col = h * TH + c;
-        if (col < p.t) atomicAdd(p.out + (int64_t)col * p.ldo + grow, p.s * (acc[c] - cmp[c]) * p.vsc[col]);
+        if (col < p.t) atomicAdd(p.out + (int64_t)col * p.ldo + grow, out_scale[col] * (acc[c] - cmp[c]));
       }
     }
   }
@@ -551,7 +584,9 @@ SymGrid sym_grid(int64_t n, int T, int num_sms) {
   const int64_t tile_bytes = (int64_t)BN * (DPH + T) * 2 * 2 + 256 + (int64_t)BN * T * 4;
   const int64_t band_l2 = std::max<int64_t>(64, (48LL << 20) / tile_bytes);
   const int64_t band_fill = g.tiles / (4LL * num_sms);
-  g.band = (int)std::max<int64_t>(2, std::min(band_l2, band_fill));
+  // even, so that every segment starts on an even column tile and the pairs
+  // of the second contraction never straddle the diagonal block
+  g.band = (int)(std::max<int64_t>(2, std::min(band_l2, band_fill)) & ~int64_t(1));
   g.segments = 0;
   for (int64_t b = 0; b * g.band < g.col_tiles; ++b) {
     const int64_t hi = std::min<int64_t>((b + 1) * g.band, g.col_tiles);

@@ -5,6 +5,8 @@ import os
 import re
 import subprocess
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -58,3 +60,30 @@ def test_product_path_has_no_fallback(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="libgp.so not found"):
         _lib.load(str(tmp_path / "missing.so"))
+
+
+def test_subset_indices_are_distinct_sorted_and_seeded():
+    """gp_subset_indices runs on the host (no GPU): M distinct sorted rows,
+    the same for the same seed, different for another seed, and every row
+    reachable."""
+    import ctypes
+    from paper_2109_09817_gb300 import _lib
+    lib = _lib.load()
+
+    def draw(N, M, seed):
+        idx = np.empty(M, dtype=np.int64)
+        assert lib.gp_subset_indices(N, M, ctypes.c_uint64(seed),
+                                     idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))) == 0
+        return idx
+
+    a = draw(1000, 300, 7)
+    assert len(np.unique(a)) == 300 and np.all(np.diff(a) > 0) and a[0] >= 0 and a[-1] < 1000
+    assert np.array_equal(a, draw(1000, 300, 7)) and not np.array_equal(a, draw(1000, 300, 8))
+    assert np.array_equal(draw(50, 50, 1), np.arange(50))
+    seen = np.zeros(20, int)
+    for s in range(400):
+        seen[draw(20, 3, s)] += 1
+    assert seen.min() > 0.5 * seen.mean()          # close to uniform over the rows
+    idx = np.empty(2, dtype=np.int64)
+    assert lib.gp_subset_indices(5, 6, ctypes.c_uint64(0),
+                                 idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))) == _lib.GP_EINVAL

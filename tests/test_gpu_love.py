@@ -114,7 +114,7 @@ def test_predict_sum_matches_oracle(gp, ctx, prec):
         mp_ref, _ = go.predict(w.X, w.y, Xm, w.lengthscale, 1.0, w.sigma2)
         prior = float(np.sum(go.kernel_matrix(Xm, Xm, w.lengthscale, 1.0)))
         assert abs(ms_e - mean_ref) <= 1e-4 * np.sum(np.abs(mp_ref)), (ms_e, mean_ref)
-        assert ms_c == ms_e
+        assert abs(ms_c - ms_e) <= 1e-6 * max(1.0, np.sum(np.abs(mp_ref)))   # FP64 atomics: order varies
         assert abs(vs_e - var_ref) <= 1e-4 * prior, (vs_e, var_ref, prior)
         cref = go.cached_variance_sum(w.X, Xm, w.lengthscale, 1.0, R)
         assert abs(vs_c - cref) <= 1e-4 * prior, (vs_c, cref, prior)

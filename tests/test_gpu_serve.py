@@ -39,8 +39,8 @@ def _oracle_cache(w):
     return R
 
 
-def _molecule_rows(w, n_occ, rng):
-    i = rng.choice(len(w.Xtest), size=n_occ, replace=False)
+def _molecule_rows(w, n_rows, rng):
+    i = rng.choice(len(w.Xtest), size=n_rows, replace=n_rows > len(w.Xtest))
     return w.Xtest[i].astype(np.float32)
 
 

@@ -155,17 +155,22 @@ def test_tc_full_size_solve_gp256k(gp, ctx):
     assert res.max() <= 1e-4, res
 
 
-@pytest.mark.parametrize("name,N,d", [("gp2k", 1500, 32), ("gp256k", 1024, 64)])
-def test_tc_backward_matches_oracle(gp, ctx, name, N, d):
+@pytest.mark.parametrize("name,N,d,npr,prec", [("gp2k", 1500, 32, 15, "split_tf32"),
+                                              ("gp256k", 1024, 64, 15, "split_tf32"),
+                                              ("gp256k", 4096, 64, 31, "split_tf32"),
+                                              ("gp256k", 4096, 64, 31, "split_f16")])
+def test_tc_backward_matches_oracle(gp, ctx, name, N, d, npr, prec):
     """Tensor-core backward (split TF32, d_pad 32 and 64) against the
-    oracle's same-probe gradient; the solve runs in split TF32 as well."""
+    oracle's same-probe gradient, the solve in the pass's precision; at N =
+    4096 with 31 probes, the oracle check of the 2^18-row gradient
+    configuration (64 lengthscales, s, sigma^2)."""
     w = make_workload(name, N=N, d=d)
     X = torch.from_numpy(w.X).cuda()
     y = torch.from_numpy(w.y).cuda()
     th = gp.Theta(w.lengthscale, 1.0, w.sigma2)
-    seed, k, npr = 4, 32, 15
+    seed, k = 4, 32
     r = gp.gp_logml_and_grad(ctx, X, th, y, n_probes=npr, seed=seed, k=k, tol=1e-6,
-                             max_iter=2000, precision=gp.GP_FP32_SPLIT_TF32,
+                             max_iter=2000, precision=gp.PRECISIONS[prec],
                              allow_notconv=True, precond=gp.GP_PC_RESID)
     L, pr, _ = go.pivoted_cholesky(w.X, w.lengthscale, 1.0, k)
     rr = go.residual_diagonal(w.X, w.lengthscale, 1.0, L, pr)

@@ -31,7 +31,7 @@ def _logml(X, y, ell, s, sig2):
 def test_dkhat_matches_finite_differences_of_K():
     X, ell, _ = _data(n=20)
     s, sig2, h = 1.3, 1e-3, 1e-6
-    mats = go.dkhat_dtheta(X, ell, s)
+    mats = list(go.dkhat_dtheta(X, ell, s))
     for j in range(len(ell)):
         ep, em = ell.copy(), ell.copy()
         ep[j] += h
