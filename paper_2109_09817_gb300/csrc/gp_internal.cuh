@@ -35,6 +35,11 @@ constexpr int kColPad = 32;    // features are padded to this (zeros)
 constexpr int kHalfCols = 64;  // width of the FP16 split feature arrays (zeros)
 constexpr int kHalfTop = 15;   // FP16 operands are scaled into [2^14, 2^15)
 constexpr int kKExp = 14;      // K entries (<= 1) are held as 2^14 K in FP16
+// the Matern polynomial's coefficients times 2^14 (exact powers of two), so
+// that 2^14 k/s = (2^14 + 2^14 ln2 u + 2^14 (ln2)^2 u^2 / 3) 2^-u
+constexpr float kP0s = 16384.f;
+constexpr float kC1s = kC1 * 16384.f;
+constexpr float kC2s = kC2 * 16384.f;
 constexpr int kMaxT = 512;
 
 // Workspace slots owned by a context.  Each grows on demand.

@@ -507,7 +507,7 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
           const float nbc = (cc & 3) == 0 ? n4.x : (cc & 3) == 1 ? n4.y : (cc & 3) == 2 ? n4.z : n4.w;
           const float u2 = fmaf(m2, __uint_as_float(s32[cc]), na + nbc);
           const float uu = sqrt_abs_approx(u2);
-          kf[c] = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx((float)kKExp - uu);
+          kf[c] = fmaf(u2, kC2s, fmaf(uu, kC1s, kP0s)) * ex2_neg_approx(uu);
         }
         if (diag) {
           const int64_t dc = grow - (col0 + h * 32 + half * 16);

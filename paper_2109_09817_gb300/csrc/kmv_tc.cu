@@ -458,7 +458,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
         // All 32 of this warp's S columns at once.  u^2 = n_a + n_b + m2 S and
         // u = sqrt(|u^2|) in one MUFU op (the modulus absorbs a u^2 rounded
         // below zero).  K is held as 2^14 K (the scale rides in the
-        // exponent, 2^(14 - u)) and split into FP16
+        // polynomial's coefficients) and split into FP16
         // hi = fp16(K) and lo = fp16(K - hi), K - hi being exact in FP32, so
         // hi + lo = K to 2^-22.  They are packed two per 32-bit column (even
         // column in the low half): K_hi of columns [32h + 16 half, +16) to
@@ -479,7 +479,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap map_r_hi, const __grid_constan
             const float nbc = (cc & 3) == 0 ? n4.x : (cc & 3) == 1 ? n4.y : (cc & 3) == 2 ? n4.z : n4.w;
             const float u2 = fmaf(m2, __uint_as_float(s32[cc]), na + nbc);
             const float uu = sqrt_abs_approx(u2);
-            kf[c] = fmaf(u2, kC2, fmaf(uu, kC1, 1.f)) * ex2_approx((float)kKExp - uu);
+            kf[c] = fmaf(u2, kC2s, fmaf(uu, kC1s, kP0s)) * ex2_neg_approx(uu);
           }
           if (diag) {
             const int64_t dc = grow - (col0 + h * 32 + half * 16);

@@ -214,6 +214,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// 2^-x on the MUFU pipe (the negation is an operand modifier of the op)
+__device__ __forceinline__ float ex2_neg_approx(float x) {
+  float y;
+  asm("{\n .reg .f32 t;\n neg.f32 t, %1;\n ex2.approx.ftz.f32 %0, t;\n}\n" : "=f"(y) : "f"(x));
+  return y;
+}
 // sqrt(|x|) on the MUFU pipe: the modulus absorbs a u^2 rounded below zero
 // and sqrt(0) = 0, so the caller needs no clamp
 __device__ __forceinline__ float sqrt_abs_approx(float x) {
