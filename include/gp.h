@@ -74,6 +74,13 @@ enum {
                              depth per MMA.  Needs d <= 64.                 */
   GP_TF32 = 3             /* tcgen05 kind::tf32, single-pass operands       */
 };
+/* No BF16 forms: a BF16 hi + lo split keeps 16 significant bits of every
+ * operand where the FP16 and TF32 splits keep 22, at the same tensor rate as
+ * FP16; an operand-rounding emulation on the 2048-row workload gives K-hat V
+ * errors of 1.3e-5 (split BF16) against 2.4e-7 (split FP16), which leaves no
+ * margin under the 2e-5 split tolerance once the tensor core's FP32
+ * accumulation (about 1e-5 at N = 2^20) is added.  Split FP16 takes the slot
+ * of split BF16, and single TF32 that of single BF16. */
 
 /* GP_HOST, OR-ed into the `precision` argument of gp_kmatmul,
  * gp_kcross_matmul and gp_logml_and_grad: their feature, vector and output

@@ -57,9 +57,11 @@ def test_roofline_fp32_is_alu_bound():
     assert r["achieved"] == pytest.approx(2.0 * n * n * 64 / 0.02 / 1e12)
 
 
-def test_stale_traffic_is_not_reported():
-    # counters taken on an earlier kernel are not carried over
-    assert bench.KMV_DRAM_BYTES.get(("gp1m", "split_f16")) is None
+def test_traffic_is_the_captured_launch():
+    # the DRAM bytes of one captured launch of the current kernel (read +
+    # write); no entry for forms whose kernels changed since a capture
+    assert bench.KMV_DRAM_BYTES[("gp1m", "split_f16")] == 3373254912 + 705990144
+    assert bench.KMV_DRAM_BYTES.get(("gp1m", "split_tf32")) is None
 
 
 def test_precision_constants_match_header():

@@ -1,6 +1,7 @@
 """GP_HOST: the product and training-pass calls with host arrays, through
-the C ABI (GPU).  The results equal the device-array calls on the same
-inputs (the same kernels run on the staged copies) and the FP64 oracle."""
+the C ABI (GPU).  The results match the device-array calls on the same
+inputs (the same kernels run on the staged copies; their atomics add in a
+varying order, so to FP32 rounding, not bitwise) and the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -36,13 +37,13 @@ def test_kmatmul_host_arrays(gp, ctx, prec):
     got = gp.gp_kmatmul_host(ctx, w.X, th, V, gp.PRECISIONS[prec])
     dev = gp.gp_kmatmul(ctx, torch.from_numpy(w.X).cuda(), th, torch.from_numpy(V).cuda(),
                         gp.PRECISIONS[prec]).cpu().numpy()
-    assert np.array_equal(got, dev)
+    assert np.max(np.abs(got - dev)) <= 1e-6 * np.max(np.abs(dev))
     ref, aref = khat_ref(w.X, V.T, w.lengthscale, 1.0, w.sigma2)
     check_kmv(got.T, ref, aref, 1e-5 if prec == "fp32" else 2e-5, prec)
     # pinned torch tensors go through the same call
     got2 = gp.gp_kmatmul_host(ctx, torch.from_numpy(w.X).pin_memory(), th,
                               torch.from_numpy(V).pin_memory(), gp.PRECISIONS[prec])
-    assert np.array_equal(got2, dev)
+    assert np.max(np.abs(got2 - dev)) <= 1e-6 * np.max(np.abs(dev))
 
 
 def test_logml_and_grad_host_arrays(gp, ctx):
@@ -52,7 +53,8 @@ def test_logml_and_grad_host_arrays(gp, ctx):
               precision=gp.GP_FP32_SPLIT_F16)
     a = gp.gp_logml_and_grad_host(ctx, w.X, th, w.y, **kw)
     b = gp.gp_logml_and_grad(ctx, torch.from_numpy(w.X).cuda(), th, torch.from_numpy(w.y).cuda(), **kw)
-    assert a["logml"] == b["logml"] and np.array_equal(a["grad"], b["grad"])
+    assert abs(a["logml"] - b["logml"]) <= 1e-6 * abs(b["logml"])
+    assert np.max(np.abs(a["grad"] - b["grad"])) <= 1e-4 * np.max(np.abs(b["grad"]))
 
 
 def test_host_flag_only_where_documented(gp, ctx):
