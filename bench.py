@@ -57,11 +57,7 @@ PRODUCTS_PER_SOLVE = {"gp1m": 99, "gp256k": 120, "gp64k": 1200, "gp2k": 60}
 # DRAM bytes (read + write) per launch of the fused K-hat V kernel from one
 # ncu capture of the current kernel, keyed by (workload, precision); an entry
 # is removed whenever the kernel changes after its capture.
-KMV_DRAM_BYTES = {
-    # kmv_sym_kernel<16> at N = 2^20, d = 64, t = 16: 3.373 GB read + 0.706 GB
-    # written in one launch (ncu dram__bytes_read.sum / write.sum, 1 pass)
-    ("gp1m", "split_f16"): 3373254912 + 705990144,
-}
+KMV_DRAM_BYTES = {}
 # TF32 dense tensor peak from the measured BF16 one, by the nominal ratio
 # 1.1 / 2.25 PFLOP/s
 TF32_PER_BF16 = 1.1 / 2.25

@@ -414,6 +414,7 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
     const float na = p.norm[grow];
     const float xs = p.xs[0];
     const float m2 = -2.f * xs * xs;
+    const float2 na2 = make_float2(na, na), m22 = make_float2(m2, m2);
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int my_tiles = (ntiles - g + 1) / 2;
     constexpr int TH = T / 2;                // outputs drained by this warp
@@ -499,31 +500,28 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
       tmem_wait_ld();
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
-        float kf[16];
+        // two entries per packed FP32x2 instruction
+        float2 kf[8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int cc = half * 16 + c;
+        for (int c2 = 0; c2 < 8; ++c2) {
+          const int cc = half * 16 + 2 * c2;
           const float4 n4 = snb[cc >> 2];
-          const float nbc = (cc & 3) == 0 ? n4.x : (cc & 3) == 1 ? n4.y : (cc & 3) == 2 ? n4.z : n4.w;
-          const float u2 = fmaf(m2, __uint_as_float(s32[cc]), na + nbc);
-          const float uu = sqrt_abs_approx(u2);
-          kf[c] = fmaf(u2, kC2s, fmaf(uu, kC1s, kP0s)) * ex2_neg_approx(uu);
+          const float2 nb = (cc & 2) ? make_float2(n4.z, n4.w) : make_float2(n4.x, n4.y);
+          kf[c2] = matern2_scaled(make_float2(__uint_as_float(s32[cc]), __uint_as_float(s32[cc + 1])), nb,
+                                  na2, m22);
         }
         if (diag) {
           const int64_t dc = grow - (col0 + h * 32 + half * 16);
           const uint32_t dmask = (dc >= 0 && dc < 16) ? (1u << (int)dc) : 0u;
 #pragma unroll
-          for (int c = 0; c < 16; ++c) kf[c] = ((dmask >> c) & 1u) ? (float)(1 << kKExp) : kf[c];
+          for (int c2 = 0; c2 < 8; ++c2) {
+            kf[c2].x = ((dmask >> (2 * c2)) & 1u) ? (float)(1 << kKExp) : kf[c2].x;
+            kf[c2].y = ((dmask >> (2 * c2 + 1)) & 1u) ? (float)(1 << kKExp) : kf[c2].y;
+          }
         }
         uint32_t hi2[8], lo2[8];
 #pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) {
-          const __half2 hv = __floats2half2_rn(kf[2 * k2], kf[2 * k2 + 1]);
-          const float2 hf = __half22float2(hv);
-          const __half2 lv = __floats2half2_rn(kf[2 * k2] - hf.x, kf[2 * k2 + 1] - hf.y);
-          hi2[k2] = *reinterpret_cast<const uint32_t*>(&hv);
-          lo2[k2] = *reinterpret_cast<const uint32_t*>(&lv);
-        }
+        for (int k2 = 0; k2 < 8; ++k2) split_h2(kf[k2], hi2[k2], lo2[k2]);
         tmem_st8(sa + half * 8, hi2);
         tmem_st8(sa + 16 + half * 8, lo2);
         // the same values into the SMEM tile: row a = r, 16-byte chunks

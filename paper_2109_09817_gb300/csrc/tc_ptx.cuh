@@ -227,6 +227,29 @@ __device__ __forceinline__ float sqrt_abs_approx(float x) {
   asm("{\n .reg .f32 t;\n abs.ftz.f32 t, %1;\n sqrt.approx.ftz.f32 %0, t;\n}\n" : "=f"(y) : "f"(x));
   return y;
 }
+// 2^14 k/s of two kernel entries of one row (columns b, b + 1) from the
+// cross term s = x~_a . x~_b in FP16-scaled units: u^2 = m2 s + (n_a + n_b),
+// u = sqrt(|u^2|), (2^14 + 2^14 ln2 u + 2^14 (ln2)^2 u^2 / 3) 2^-u.  The
+// FP32 steps run as packed FP32x2 instructions (two entries per
+// instruction, each lane rounded to nearest as the scalar ops are); the
+// square roots and exponentials stay on the MUFU pipe.
+__device__ __forceinline__ float2 matern2_scaled(float2 s, float2 nb, float2 na2, float2 m22) {
+  const float2 u2 = __ffma2_rn(m22, s, __fadd2_rn(na2, nb));
+  const float2 uu = make_float2(sqrt_abs_approx(u2.x), sqrt_abs_approx(u2.y));
+  float2 p = __ffma2_rn(uu, make_float2(kC1s, kC1s), make_float2(kP0s, kP0s));
+  p = __ffma2_rn(u2, make_float2(kC2s, kC2s), p);
+  return __fmul2_rn(p, make_float2(ex2_neg_approx(uu.x), ex2_neg_approx(uu.y)));
+}
+// FP16 hi and lo parts of two values, packed two per 32-bit word (first
+// value in the low half): hi = fp16(v), lo = fp16(v - hi), v - hi exact in
+// FP32, so hi + lo = v to 2^-22.
+__device__ __forceinline__ void split_h2(float2 v, uint32_t& hi, uint32_t& lo) {
+  const __half2 hv = __floats2half2_rn(v.x, v.y);
+  const float2 r = __ffma2_rn(__half22float2(hv), make_float2(-1.f, -1.f), v);
+  const __half2 lv = __floats2half2_rn(r.x, r.y);
+  hi = *reinterpret_cast<const uint32_t*>(&hv);
+  lo = *reinterpret_cast<const uint32_t*>(&lv);
+}
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
