@@ -7,7 +7,7 @@
 // a range of 64-column tiles J.  For each J:
 //   S   = X~_I X~_J^T                      (FFMA, d-chunks of 32 staged in smem)
 //   K   = matern(|x~_a|^2 + |x~_b|^2 - 2 S) (FP32 + 2 MUFU per entry)
-//   O_I += K V_J                            (FFMA from a transposed K tile)
+//   O_I += K V_J                            (packed FFMA2 from a transposed K tile)
 // O is flushed with one atomic add per output element per CTA (several CTAs
 // share a row tile so that the grid fills the GPU).
 #include <algorithm>
@@ -143,21 +143,24 @@ kmv_plain_kernel(const float* __restrict__ xr, const float* __restrict__ nr,
       *reinterpret_cast<float4*>(sKT + cc * SKS + ty * 8 + 4) = make_float4(kv[4], kv[5], kv[6], kv[7]);
     }
     __syncthreads();
-    float tile_o[8][QN];
+    // the contraction with V_J, two rows per packed FP32x2 instruction
+    float2 tile_o[4][QN];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int q = 0; q < QN; ++q) tile_o[i][q] = 0.f;
+      for (int q = 0; q < QN; ++q) tile_o[i][q] = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int b = 0; b < BN; ++b) {
       const float4 k0 = *reinterpret_cast<const float4*>(sKT + b * SKS + ty * 8);
       const float4 k1 = *reinterpret_cast<const float4*>(sKT + b * SKS + ty * 8 + 4);
-      const float kr[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+      const float2 kr[4] = {make_float2(k0.x, k0.y), make_float2(k0.z, k0.w), make_float2(k1.x, k1.y),
+                            make_float2(k1.z, k1.w)};
 #pragma unroll
       for (int q = 0; q < QN; ++q) {
         const float v = sVT[(tx + 16 * q) * (BN + 1) + b];
+        const float2 v2 = make_float2(v, v);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) tile_o[i][q] = fmaf(kr[i], v, tile_o[i][q]);
+        for (int i = 0; i < 4; ++i) tile_o[i][q] = __ffma2_rn(kr[i], v2, tile_o[i][q]);
       }
     }
     // compensated (Kahan) running sum of the per-tile partial sums: over
@@ -166,7 +169,8 @@ kmv_plain_kernel(const float* __restrict__ xr, const float* __restrict__ nr,
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int q = 0; q < QN; ++q) {
-        const float yv = tile_o[i][q] - acc_c[i][q];
+        const float to = (i & 1) ? tile_o[i >> 1][q].y : tile_o[i >> 1][q].x;
+        const float yv = to - acc_c[i][q];
         const float tv = acc_o[i][q] + yv;
         acc_c[i][q] = (tv - acc_o[i][q]) - yv;
         acc_o[i][q] = tv;
