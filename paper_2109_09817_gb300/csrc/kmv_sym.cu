@@ -211,7 +211,7 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
   uint64_t* bar_fin = bar_de + DP;         // the three MMA issuers drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + Ly::NBAR);
   __shared__ int fail;
-  __shared__ float out_scale[T];           // s 2^-(e_c + 14) per output vector
+  __shared__ __align__(16) float out_scale[T];   // s 2^-(e_c + 14) per output vector
 
   int I, jt0, jt1;
   if (!segment_of(p, blockIdx.x, &I, &jt0, &jt1)) return;
@@ -468,12 +468,21 @@ kmv_sym_kernel(const __grid_constant__ CUtensorMap map_c_hi, const __grid_consta
           tmem_ld8(da + T + c8, rx);
           tmem_wait_ld();
           if (live) {
+            // the 8 output factors in two vector loads; a full chunk of
+            // vectors (t = T) takes no per-column bound
+            const float4 sc0 = reinterpret_cast<const float4*>(out_scale)[(h * TH + c8) >> 2];
+            const float4 sc1 = reinterpret_cast<const float4*>(out_scale)[((h * TH + c8) >> 2) + 1];
+            const float scv[8] = {sc0.x, sc0.y, sc0.z, sc0.w, sc1.x, sc1.y, sc1.z, sc1.w};
+            float* o = p.out + (int64_t)(h * TH + c8) * p.ldo + bcol;
+            if (p.t == T) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const int col = h * TH + c8 + c;
-              if (col < p.t)
-                atomicAdd(p.out + (int64_t)col * p.ldo + bcol,
-                          out_scale[col] * (__uint_as_float(rr[c]) + __uint_as_float(rx[c])));
+              for (int c = 0; c < 8; ++c)
+                atomicAdd(o + c * p.ldo, scv[c] * (__uint_as_float(rr[c]) + __uint_as_float(rx[c])));
+            } else {
+#pragma unroll
+              for (int c = 0; c < 8; ++c)
+                if (h * TH + c8 + c < p.t)
+                  atomicAdd(o + c * p.ldo, scv[c] * (__uint_as_float(rr[c]) + __uint_as_float(rx[c])));
             }
           }
         }

@@ -221,10 +221,12 @@ __device__ __forceinline__ float ex2_neg_approx(float x) {
   return y;
 }
 // sqrt(|x|) on the MUFU pipe: the modulus absorbs a u^2 rounded below zero
-// and sqrt(0) = 0, so the caller needs no clamp
+// and sqrt(0) = 0, so the caller needs no clamp.  The modulus is the plain
+// (non-flushing) abs, which rides on the MUFU operand as a modifier; the
+// square root's own ftz flushes a subnormal |x| to 0.
 __device__ __forceinline__ float sqrt_abs_approx(float x) {
   float y;
-  asm("{\n .reg .f32 t;\n abs.ftz.f32 t, %1;\n sqrt.approx.ftz.f32 %0, t;\n}\n" : "=f"(y) : "f"(x));
+  asm("{\n .reg .f32 t;\n abs.f32 t, %1;\n sqrt.approx.ftz.f32 %0, t;\n}\n" : "=f"(y) : "f"(x));
   return y;
 }
 // 2^14 k/s of two kernel entries of one row (columns b, b + 1) from the
@@ -242,12 +244,18 @@ __device__ __forceinline__ float2 matern2_scaled(float2 s, float2 nb, float2 na2
 }
 // FP16 hi and lo parts of two values, packed two per 32-bit word (first
 // value in the low half): hi = fp16(v), lo = fp16(v - hi), v - hi exact in
-// FP32, so hi + lo = v to 2^-22.
+// FP32, so hi + lo = v to 2^-22.  v - hi is one mixed-precision FMA per
+// value (FP16 hi times FP16 -1 plus the FP32 v, rounded once), so hi is
+// never widened back to FP32 by a separate conversion.
 __device__ __forceinline__ void split_h2(float2 v, uint32_t& hi, uint32_t& lo) {
   const __half2 hv = __floats2half2_rn(v.x, v.y);
-  const float2 r = __ffma2_rn(__half22float2(hv), make_float2(-1.f, -1.f), v);
-  const __half2 lv = __floats2half2_rn(r.x, r.y);
   hi = *reinterpret_cast<const uint32_t*>(&hv);
+  float r0, r1;
+  asm("{\n .reg .b16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
+      " fma.rn.f32.f16 %0, a, m, %3;\n fma.rn.f32.f16 %1, b, m, %4;\n}\n"
+      : "=f"(r0), "=f"(r1)
+      : "r"(hi), "f"(v.x), "f"(v.y));
+  const __half2 lv = __floats2half2_rn(r0, r1);
   lo = *reinterpret_cast<const uint32_t*>(&lv);
 }
 __device__ __forceinline__ float rsqrt_approx(float x) {
