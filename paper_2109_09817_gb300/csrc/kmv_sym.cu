@@ -49,7 +49,7 @@ constexpr int BN = 64;
 constexpr int NTHREADS = 640;
 constexpr int EPI_WARP0 = 4;
 constexpr int GROUP_WARPS = 8;
-constexpr int OGROUP = 2;       // a group's tiles accumulated in TMEM per O_I drain
+constexpr int OGROUP = 4;       // a group's tiles accumulated in TMEM per O_I drain
 constexpr int DPH = kHalfCols;  // FP16 features per row: one 128-byte box
 
 template <int T>
