@@ -57,7 +57,11 @@ PRODUCTS_PER_SOLVE = {"gp1m": 99, "gp256k": 120, "gp64k": 1200, "gp2k": 60}
 # DRAM bytes (read + write) per launch of the fused K-hat V kernel from one
 # ncu capture of the current kernel, keyed by (workload, precision); an entry
 # is removed whenever the kernel changes after its capture.
-KMV_DRAM_BYTES = {}
+KMV_DRAM_BYTES = {
+    # kmv_sym_kernel<16> at N = 2^20, d = 64, t = 16: 3.344 GB read + 0.669 GB
+    # written in one launch (ncu dram__bytes_read.sum / write.sum, 1 pass)
+    ("gp1m", "split_f16"): 3344414208 + 668886528,
+}
 # TF32 dense tensor peak from the measured BF16 one, by the nominal ratio
 # 1.1 / 2.25 PFLOP/s
 TF32_PER_BF16 = 1.1 / 2.25

@@ -60,6 +60,7 @@ def test_roofline_fp32_is_alu_bound():
 def test_traffic_is_the_captured_launch():
     # the DRAM bytes of one captured launch of the current kernel (read +
     # write); no entry for forms whose kernels changed since a capture
+    assert bench.KMV_DRAM_BYTES[("gp1m", "split_f16")] == 3344414208 + 668886528
     for key, v in bench.KMV_DRAM_BYTES.items():
         assert key[0] in bench.WORKLOADS and key[1] in ("split_f16", "split_tf32", "fp32")
         assert isinstance(v, int) and v > 0
