@@ -660,8 +660,10 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
                               const CgScal* sc, double* rzpart) {
   const int k = pc ? pc->k : 0;
   if (k > 0 && pc->dh64 && pc->L) {
-    // FP64 path (see ltr64_kernel)
-    const int nb = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 2048)));
+    // FP64 path (see ltr64_kernel).  Row chunks of at least 256 rows, up to
+    // two CTAs per SM: the FP64 pipe is narrow on this GPU, so the apply is
+    // compute-bound and needs every SM even at N = 65,536.
+    const int nb = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 256)));
     double* part = ws<double>(ctx, WS_CG_G, (size_t)nb * k * t + (size_t)k * t);
     double* w64 = ws<double>(ctx, WS_CG_W64, (size_t)k * t);
     if (!part || !w64) return set_err(ctx, GP_ENOMEM, "workspace (precond)");
