@@ -240,6 +240,21 @@ GP_API int gp_mbcg(gp_ctx* ctx, const float* X, int64_t N, int d,
             double* alpha_hist, double* beta_hist, int* iters,
             double* rel_resid);
 
+/* Lanczos quadrature of mBCG's coefficients (Sec. 3.2: the log-determinant
+ * term of Eq. ll).  For each column c, T_c is the iters[c] x iters[c]
+ * tridiagonal of the PCG/Lanczos relation, T_jj = 1/alpha_j +
+ * beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j, and
+ * quad[c] = e1^T log(T_c) e1 (0 when iters[c] = 0); the log-determinant
+ * estimate is log|P| + (1/t) sum_c ||z_c||^2_{P^{-1}} quad[c] over the probe
+ * columns.  alpha_hist, beta_hist: device FP64, max_iter*t, entry [j*t + c]
+ * (the layout gp_mbcg writes); iters: HOST, t ints in [0, max_iter];
+ * quad: HOST, t doubles.  1 <= t <= 256.  Computed on the device to about
+ * 1e-13 absolute (a trapezoid rule on an integral representation, no
+ * eigendecomposition).  GP_EBREAKDOWN if some T_c is not positive definite
+ * (its quad[c] is 0).  Synchronises. */
+GP_API int gp_lanczos_logquad(gp_ctx* ctx, const double* alpha_hist, const double* beta_hist, int t,
+                              int max_iter, const int* iters, double* quad);
+
 /* AltBBMM solve (Sec. 3.2): block CG (Sec. 3.1, BCG) on the symmetrically
  * preconditioned system S^T K-hat S W = S^T B, Omega = S W, with S S^T =
  * P^{-1}, P = L L^T + D the Nystrom preconditioner whose landmarks are the

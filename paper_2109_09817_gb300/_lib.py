@@ -22,6 +22,7 @@ GP_HOST = 0x100
 EXPORTS = (
     "gp_create", "gp_destroy", "gp_set_stream", "gp_sync", "gp_last_error",
     "gp_launch_count", "gp_set_option", "gp_profile", "gp_profile_read", "gp_kmatmul", "gp_kcross_matmul", "gp_pivchol", "gp_mbcg",
+    "gp_lanczos_logquad",
     "gp_mbcg_refine", "gp_bcg", "gp_logml_and_grad", "gp_model_fit", "gp_model_free", "gp_predict",
     "gp_model_variance_cache", "gp_predict_sum", "gp_subset_indices", "gp_hyperopt", "gp_train",
     "gp_kmatmul_noalloc", "gp_server_create", "gp_server_add_model", "gp_server_predict", "gp_server_molecule",
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH):
         "gp_pivchol": (c_int, [vp, vp, i64, c_int, th, c_int, vp, vp, ip, vp]),
         "gp_mbcg": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, vp, c_int, c_dbl, c_int,
                             c_int, c_int, vp, vp, vp, ip, dp]),
+        "gp_lanczos_logquad": (c_int, [vp, vp, vp, c_int, c_int, ip, dp]),
         "gp_bcg": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, vp, c_int, c_dbl, c_int, c_int,
                            vp, ip, dp]),
         "gp_mbcg_refine": (c_int, [vp, vp, i64, c_int, th, vp, c_int, vp, vp, c_int, c_dbl,

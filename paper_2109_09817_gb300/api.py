@@ -219,6 +219,24 @@ def gp_mbcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tenso
                 relres=np.array(rr[:]), rc=rc)
 
 
+def gp_lanczos_logquad(ctx: Context, alpha: torch.Tensor, beta: torch.Tensor, iters) -> np.ndarray:
+    """e1^T log(T_c) e1 for each column c of mBCG's coefficient histories
+    (alpha, beta: (max_iter, t) float64 on the device, as gp_mbcg returns
+    them; iters: t step counts).  Returns a float64 array of t."""
+    _dev(ctx, alpha, torch.float64, "alpha")
+    _dev(ctx, beta, torch.float64, "beta")
+    if alpha.shape != beta.shape or alpha.dim() != 2:
+        raise ValueError("alpha and beta must be (max_iter, t) arrays of one shape")
+    max_iter, t = alpha.shape
+    it = np.asarray(iters, dtype=np.int64).reshape(-1)
+    if it.shape[0] != t:
+        raise ValueError("iters must hold one count per column")
+    ci = (ctypes.c_int * t)(*[int(v) for v in it])
+    q = (ctypes.c_double * t)()
+    ctx.check(ctx.lib.gp_lanczos_logquad(ctx.h, _p(alpha), _p(beta), t, max_iter, ci, q))
+    return np.array(q[:])
+
+
 def gp_bcg(ctx: Context, X: torch.Tensor, theta: Theta, L: Optional[torch.Tensor],
            B: torch.Tensor, tol: float = 1e-4, max_iter: int = 1000,
            precision: int = GP_FP32_SPLIT_TF32, resid: Optional[torch.Tensor] = None,
