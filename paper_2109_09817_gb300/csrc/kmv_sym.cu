@@ -55,12 +55,15 @@ constexpr int DPH = kHalfCols;  // FP16 features per row: one 128-byte box
 template <int T>
 struct SymLayout {
   // S/K buffers (TMEM and SMEM), an even number: the tiles of a pair sit in
-  // adjacent buffers, so that one MN-major descriptor spans both
-  static constexpr int NSB = T <= 16 ? 4 : 2;
-  static constexpr int XS = T <= 16 ? 3 : 4;     // X~_J ring slots
+  // adjacent buffers, so that one MN-major descriptor spans both.  Four
+  // buffers (two pairs in flight) at both T; at T = 32 the TMEM budget then
+  // leaves one O_I accumulator per group and one pair D, and shared memory
+  // two X~_J slots.
+  static constexpr int NSB = 4;
+  static constexpr int XS = T <= 16 ? 3 : 2;     // X~_J ring slots
   static constexpr int VS = 4;                   // V_J ring slots
   static constexpr int OB = T <= 16 ? 2 : 1;     // O_I accumulators per epilogue group
-  static constexpr int DP = 2;                   // pair D accumulators (M = 128, 2T columns)
+  static constexpr int DP = T <= 16 ? 2 : 1;     // pair D accumulators (M = 128, 2T columns)
   static constexpr int XJ_BOX = BN * 128;        // 64 rows x 128 B
   static constexpr int V_BOX = T * 128;          // T vectors x 64 FP16 columns
   static constexpr int KT = BM * 128;            // one K part: 128 rows a x 64 columns b, FP16
