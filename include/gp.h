@@ -266,7 +266,12 @@ GP_API int gp_lanczos_logquad(gp_ctx* ctx, const double* alpha_hist, const doubl
  * (GP_EINVAL).  iters (host int, nullable): block steps taken; rel_resid
  * (host t doubles, nullable).  The s x s systems are solved by pseudo-inverse
  * (directions below 1e-10 of the largest eigenvalue are dropped), so columns
- * that converge or become dependent get zero steps.  GP_ENOTCONV after
+ * that converge or become dependent get zero steps.  In FP32 storage the
+ * block recurrence can stall a little above a tight tol (for example at
+ * 1.1e-5 on 2048 points with D = sigma^2 I); when the largest residual is
+ * within 4 tol and has not fallen by 10 % over 3 steps, the residual is
+ * recomputed as B - K-hat Omega (one more product) and the recurrence
+ * restarts from the current iterate, at most twice.  GP_ENOTCONV after
  * max_iter steps (Omega holds the last iterate); GP_EBREAKDOWN if a block
  * Gram matrix vanishes.
  * Synchronises every step. */

@@ -1,7 +1,13 @@
 """AltBBMM block CG (gp_bcg) against the FP64 oracle's block CG and the
-Cholesky solution, through the C ABI.  Gates: true relative residual 1e-4
-(the solve tolerance), solution vs Cholesky 1e-3, block steps within 25 % + 3
-of the oracle's FP64 block CG on the same preconditioner."""
+Cholesky solution, through the C ABI.  Gates: true relative residual 1e-4,
+solution vs Cholesky 1e-3, block steps within 25 % + 3 of the oracle's FP64
+block CG on the same preconditioner and tolerance.
+
+The step comparison runs above the FP32 floor of each preconditioner form:
+with D = sigma^2 I the FP32 block recurrence on gp2k stalls near 1.1e-5 in
+about one solve in twenty (the block loses conjugacy), so that form is
+compared at tol 2e-5; below the floor the solver's residual-replacement
+restart takes over, tested on its own (test_bcg_restart_below_fp32_floor)."""
 import numpy as np
 import pytest
 
@@ -32,8 +38,8 @@ def _theta(gp, w):
     return gp.Theta(w.lengthscale, w.outputscale, w.sigma2)
 
 
-@pytest.mark.parametrize("resid", [False, True])
-def test_bcg_gp2k_matches_oracle(gp, ctx, resid):
+@pytest.mark.parametrize("resid,tol", [(False, 2e-5), (True, 1e-5)])
+def test_bcg_gp2k_matches_oracle(gp, ctx, resid, tol):
     w = make_workload("gp2k")
     X = torch.from_numpy(w.X).cuda()
     th = _theta(gp, w)
@@ -43,8 +49,8 @@ def test_bcg_gp2k_matches_oracle(gp, ctx, resid):
     res_d = out[3] if resid else None
     rng = np.random.default_rng(6)
     B = np.vstack([w.y, rng.choice([-1.0, 1.0], size=(15, w.N))]).astype(np.float32)
-    r = gp.gp_bcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=1e-5, max_iter=500, resid=res_d)
-    assert r["rc"] == 0 and np.all(r["relres"] < 1e-5)
+    r = gp.gp_bcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=tol, max_iter=500, resid=res_d)
+    assert r["rc"] == 0 and np.all(r["relres"] < tol)
     Om = r["Omega"].cpu().numpy().T.astype(np.float64)
     true = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
     assert true.max() <= 1e-4
@@ -55,8 +61,29 @@ def test_bcg_gp2k_matches_oracle(gp, ctx, resid):
     Lr, pr, _ = go.pivoted_cholesky(w.X, w.lengthscale, 1.0, k)
     rr = go.residual_diagonal(w.X, w.lengthscale, 1.0, Lr, pr) if resid else None
     o = go.bcg(lambda V: Kh @ V, B.T.astype(np.float64), go.sym_precond_factor(Lr, w.sigma2, rr),
-               1e-5, 500)
+               tol, 500)
     assert abs(r["iters"] - o["iters"]) <= 0.25 * o["iters"] + 3, (r["iters"], o["iters"])
+
+
+def test_bcg_restart_below_fp32_floor(gp, ctx):
+    """tol 3e-6 with D = sigma^2 I is below where the FP32 block recurrence
+    stalls (about 1.1e-5 on gp2k): the solve converges through the
+    residual-replacement restart instead of running to max_iter."""
+    w = make_workload("gp2k")
+    X = torch.from_numpy(w.X).cuda()
+    th = _theta(gp, w)
+    L = gp.gp_pivchol(ctx, X, th, 32)[0]
+    rng = np.random.default_rng(6)
+    B = np.vstack([w.y, rng.choice([-1.0, 1.0], size=(15, w.N))]).astype(np.float32)
+    r = gp.gp_bcg(ctx, X, th, L, torch.from_numpy(B).cuda(), tol=3e-6, max_iter=200)
+    assert r["rc"] == 0 and np.all(r["relres"] < 3e-6)
+    Om = r["Omega"].cpu().numpy().T.astype(np.float64)
+    true = go.true_relative_residual(w.X, w.lengthscale, 1.0, w.sigma2, Om, B.T)
+    assert true.max() <= 2e-5
+    Kh = go.khat_matrix(w.X, w.lengthscale, 1.0, w.sigma2)
+    ref = go.cholesky_solve(Kh, B.T.astype(np.float64))
+    err = np.linalg.norm(Om - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= 1e-3
 
 
 def test_bcg_block_of_one_is_pcg(gp, ctx):
