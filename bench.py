@@ -53,7 +53,7 @@ WORKLOADS = {
 }
 # K-hat products one solve of each workload needs (split forms, seed 0);
 # the reference arm scales its per-product oracle time by this count.
-PRODUCTS_PER_SOLVE = {"gp1m": 99, "gp256k": 120, "gp64k": 1200, "gp2k": 60}
+PRODUCTS_PER_SOLVE = {"gp1m": 108, "gp256k": 74, "gp64k": 1217, "gp2k": 60}
 # DRAM bytes (read + write) per launch of the fused K-hat V kernel from one
 # ncu capture of the current kernel, keyed by (workload, precision); an entry
 # is removed whenever the kernel changes after its capture.
