@@ -211,59 +211,89 @@ __global__ void z_apply_kernel(const float* __restrict__ L32, int64_t ldl, int k
   }
 }
 
-// ---- FP64 Woodbury apply ------------------------------------------------------
+// ---- Woodbury apply in float-float arithmetic -----------------------------------
 // Z = P^{-1} R = dh o (dh o R - Lt w), w = C^{-1} Lt^T (dh o R), Lt = dh o L.
 // In the dominant directions of L L^T the result is (1 + lambda) times smaller
 // than dh o R, so an FP32 evaluation loses log10(1 + lambda) digits (~7 for
-// sigma^2 = 1e-4); both row passes therefore run in FP64 from the FP64 factor
-// L (row j contiguous, ld n) and dh64.
-//
-// part[(b * k + j) * t + c] = sum over rows of block b of L[j] dh^2 R_c, a
-// k x 64-row by 64-row x t product per staged tile.  grid (blocks,
+// sigma^2 = 1e-4).  Both row passes therefore carry about 44 significant
+// bits: the FP64 factor L and D^{-1} = dh^2 are split once into FP32 pairs
+// hi + lo (hi = fl32(v), lo = fl32(v - hi)), and every multiply-add is a
+// float-float operation on the FP32 pipes: the product's rounding error is
+// recovered exactly by an FMA (Dekker's two-product), the sum's by Knuth's
+// two-sum, and the cross terms a_hi b_lo + a_lo b_hi ride in the low word.
+// Each step is an explicitly rounded intrinsic, so the compiler cannot fuse
+// or reorder it.  On this GPU the FP32 pipes issue about 64 times the FP64
+// rate, so the 11 FP32 instructions of one float-float multiply-add still
+// beat one FP64 FMA several times over.
+
+// (sh, sl) += (ah, al) (bh, bl)
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = s;
+}
+
+// part[(b * k + j) * t + c] = sum over rows of block b of L[j] dh^2 R_c: per
+// stage a 64-pivot-row x 32-row tile of L times a 32-row x t tile of R.  grid (blocks,
 // ceil(k / 64), ceil(t / CW)), 256 threads: lane l of warp w owns column
 // c0 + l % CW and the pivot rows j0 + (32 / CW) w + l / CW + 8 (32 / CW) m,
-// so each block reads its rows of R once per 64 pivot rows and every FMA is
-// a useful one (CW = 16 for t <= 16).
+// so each block reads its rows of R once per 64 pivot rows and every
+// multiply-add is a useful one (CW = 16 for t <= 16).
 template <int CW>
-__global__ void __launch_bounds__(256) ltr64_kernel(const double* __restrict__ L, int64_t ldl, int k,
-                                                    const float* __restrict__ R, int64_t ldr, int t, int64_t n,
-                                                    const CgScal* __restrict__ sc, const double* __restrict__ dh,
-                                                    double* __restrict__ part) {
+__global__ void __launch_bounds__(256) ltr_ff_kernel(const float* __restrict__ Lh, const float* __restrict__ Ll,
+                                                     int64_t ldl, int k, const float* __restrict__ R, int64_t ldr,
+                                                     int t, int64_t n, const CgScal* __restrict__ sc,
+                                                     const float* __restrict__ d2h, const float* __restrict__ d2l,
+                                                     double* __restrict__ part) {
   constexpr int JPW = 32 / CW;          // pivot rows per warp and step
   constexpr int M = 64 / (8 * JPW);     // accumulators per thread
-  __shared__ double Rs[32][CW + 1];     // [row][column], dh^2 folded in
-  __shared__ double Ls[64][33];         // [pivot row][row]
+  __shared__ float Rsh[32][CW + 1], Rsl[32][CW + 1];   // [row][column], dh^2 folded in
+  __shared__ float Lsh[64][33], Lsl[64][33];           // [pivot row][row]
   const int j0 = blockIdx.y * 64, c0 = blockIdx.z * CW;
   const int nc = min(CW, t - c0), nj = min(64, k - j0);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cl = lane % CW, jl = w * JPW + lane / CW;
-  double acc[M];
+  float acch[M], accl[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) acc[m] = 0.0;
+  for (int m = 0; m < M; ++m) {
+    acch[m] = 0.f;
+    accl[m] = 0.f;
+  }
   const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
   const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
   for (int64_t a0 = r0; a0 < r1; a0 += 32) {
     for (int idx = threadIdx.x; idx < 32 * CW; idx += 256) {
       const int cc = idx >> 5, aa = idx & 31;
       const int64_t a = a0 + aa;
-      double v = 0.0;
+      float vh = 0.f, vl = 0.f;
       if (cc < nc && a < r1) {
-        const double d = dh[a];
-        v = (double)R[(int64_t)(c0 + cc) * ldr + a] * d * d;
+        const float r = R[(int64_t)(c0 + cc) * ldr + a];
+        vh = __fmul_rn(r, d2h[a]);
+        vl = __fmaf_rn(r, d2l[a], __fmaf_rn(r, d2h[a], -vh));
       }
-      Rs[aa][cc] = v;
+      Rsh[aa][cc] = vh;
+      Rsl[aa][cc] = vl;
     }
     for (int idx = threadIdx.x; idx < 64 * 32; idx += 256) {
       const int jj = idx >> 5, aa = idx & 31;
       const int64_t a = a0 + aa;
-      Ls[jj][aa] = (jj < nj && a < r1) ? L[(int64_t)(j0 + jj) * ldl + a] : 0.0;
+      const bool in = jj < nj && a < r1;
+      Lsh[jj][aa] = in ? Lh[(int64_t)(j0 + jj) * ldl + a] : 0.f;
+      Lsl[jj][aa] = in ? Ll[(int64_t)(j0 + jj) * ldl + a] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
     for (int aa = 0; aa < 32; ++aa) {
-      const double r = Rs[aa][cl];
+      const float rh = Rsh[aa][cl], rl = Rsl[aa][cl];
 #pragma unroll
-      for (int m = 0; m < M; ++m) acc[m] = fma(Ls[jl + 8 * JPW * m][aa], r, acc[m]);
+      for (int m = 0; m < M; ++m)
+        ff_mac(acch[m], accl[m], Lsh[jl + 8 * JPW * m][aa], Lsl[jl + 8 * JPW * m][aa], rh, rl);
     }
     __syncthreads();
   }
@@ -272,7 +302,8 @@ __global__ void __launch_bounds__(256) ltr64_kernel(const double* __restrict__ L
     const int j = j0 + jl + 8 * JPW * m;
     if (j < k && cl < nc) {
       const int c = c0 + cl;
-      part[((int64_t)blockIdx.x * k + j) * t + c] = (sc && !sc[c].active) ? 0.0 : acc[m];
+      part[((int64_t)blockIdx.x * k + j) * t + c] =
+          (sc && !sc[c].active) ? 0.0 : (double)acch[m] + (double)accl[m];
     }
   }
 }
@@ -288,21 +319,28 @@ __global__ void w64_apply_kernel(const double* __restrict__ Cinv, const double* 
   w[idx] = s;
 }
 
-// Z_c = dh o (dh o R_c - dh o sum_j L_j w_jc) in FP64 on NC-column chunks
-// (NC = 16 for t <= 16), rz partials.  One row per thread, the k x NC chunk
-// of w in shared memory (broadcast reads).
+// Z_c = dh^2 o (R_c - sum_j L_j w_jc) in float-float on NC-column chunks
+// (NC = 16 for t <= 16), and the FP64 partials of R_c^T Z_c.  One row per
+// thread; the k x NC chunk of w, split into FP32 pairs, in shared memory
+// (broadcast reads).
 template <int NC>
-__global__ void __launch_bounds__(256, NC == 16 ? 2 : 1) z64_apply_kernel(const double* __restrict__ L, int64_t ldl, int k,
-                                 const double* __restrict__ w, int t, const float* __restrict__ R,
-                                 float* __restrict__ Z, int64_t ld, int64_t n, const double* __restrict__ dh,
-                                 const CgScal* __restrict__ sc, double* __restrict__ rzpart) {
-  extern __shared__ double sw64[];   // k x NC chunk of w
+__global__ void __launch_bounds__(256, NC == 16 ? 2 : 1) z_ff_kernel(
+    const float* __restrict__ Lh, const float* __restrict__ Ll, int64_t ldl, int k, const double* __restrict__ w,
+    int t, const float* __restrict__ R, float* __restrict__ Z, int64_t ld, int64_t n,
+    const float* __restrict__ d2h, const float* __restrict__ d2l, const CgScal* __restrict__ sc,
+    double* __restrict__ rzpart) {
+  extern __shared__ float swf[];   // k x NC hi parts, then k x NC lo parts
   __shared__ double sh[32];
   const int c0 = blockIdx.y * NC;
   const int nc = min(NC, t - c0);
+  float* swh = swf;
+  float* swl = swf + k * NC;
   for (int idx = threadIdx.x; idx < k * NC; idx += blockDim.x) {
     const int j = idx / NC, cc = idx % NC;
-    sw64[idx] = cc < nc ? w[j * t + c0 + cc] : 0.0;
+    const double v = cc < nc ? w[j * t + c0 + cc] : 0.0;
+    const float vh = (float)v;
+    swh[idx] = vh;
+    swl[idx] = (float)(v - (double)vh);
   }
   __syncthreads();
   bool act[NC];
@@ -315,23 +353,32 @@ __global__ void __launch_bounds__(256, NC == 16 ? 2 : 1) z64_apply_kernel(const 
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) rz[cc] = 0.0;
   for (int64_t a = r0 + threadIdx.x; a < r1; a += blockDim.x) {
-    const double d = dh[a];
-    double acc[NC];
+    float acch[NC], accl[NC];
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) acc[cc] = 0.0;
-    for (int j = 0; j < k; ++j) {
-      const double l = L[(int64_t)j * ldl + a];
-#pragma unroll
-      for (int cc = 0; cc < NC; ++cc) acc[cc] = fma(l, sw64[j * NC + cc], acc[cc]);
+    for (int cc = 0; cc < NC; ++cc) {
+      acch[cc] = 0.f;
+      accl[cc] = 0.f;
     }
+    for (int j = 0; j < k; ++j) {
+      const float lh = Lh[(int64_t)j * ldl + a], ll = Ll[(int64_t)j * ldl + a];
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) ff_mac(acch[cc], accl[cc], lh, ll, swh[j * NC + cc], swl[j * NC + cc]);
+    }
+    const float qh = d2h[a], ql = d2l[a];
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) {
       if (!act[cc]) continue;
       const int64_t o = (int64_t)(c0 + cc) * ld + a;
       const float r = R[o];
-      const double z = d * d * ((double)r - acc[cc]);
-      Z[o] = (float)z;
-      rz[cc] += (double)r * z;
+      // (dh, dl) = r - acc, exactly up to the low word
+      const float s = __fsub_rn(r, acch[cc]);
+      const float bb = __fsub_rn(s, r);
+      const float dl = __fsub_rn(__fadd_rn(__fsub_rn(r, __fsub_rn(s, bb)), __fsub_rn(-acch[cc], bb)), accl[cc]);
+      // z = dh^2 (s + dl)
+      const float zh = __fmul_rn(s, qh);
+      const float zl = __fmaf_rn(dl, qh, __fmaf_rn(s, ql, __fmaf_rn(s, qh, -zh)));
+      Z[o] = __fadd_rn(zh, zl);
+      rz[cc] += (double)r * ((double)zh + (double)zl);
     }
   }
   if (rzpart) {
@@ -659,21 +706,26 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
                               const float* R, float* Z, int64_t ld, int t,
                               const CgScal* sc, double* rzpart) {
   const int k = pc ? pc->k : 0;
-  if (k > 0 && pc->dh64 && pc->L) {
-    // FP64 path (see ltr64_kernel).  Row chunks of at least 256 rows, up to
-    // two CTAs per SM: the FP64 pipe is narrow on this GPU, so the apply is
-    // compute-bound and needs every SM even at N = 65,536.
+  if (k > 0 && pc->Lff && pc->d2ff) {
+    // float-float path (see ltr_ff_kernel).  Row chunks of at least 256
+    // rows, up to two CTAs per SM: the apply is compute-bound and needs every
+    // SM even at N = 65,536.
+    const int64_t ldf = pc->ld32;
+    const float* Lh = pc->Lff;
+    const float* Ll = pc->Lff + (size_t)k * ldf;
+    const float* d2h = pc->d2ff;
+    const float* d2l = pc->d2ff + ldf;
     const int nb = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, ceil_div(n, 256)));
     double* part = ws<double>(ctx, WS_CG_G, (size_t)nb * k * t + (size_t)k * t);
     double* w64 = ws<double>(ctx, WS_CG_W64, (size_t)k * t);
     if (!part || !w64) return set_err(ctx, GP_ENOMEM, "workspace (precond)");
     double* G = part + (size_t)nb * k * t;
     if (t <= 16)
-      ltr64_kernel<16><<<dim3(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 16)), 256, 0, ctx->stream>>>(
-          pc->L, pc->n, k, R, ld, t, n, sc, pc->dh64, part);
+      ltr_ff_kernel<16><<<dim3(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 16)), 256, 0, ctx->stream>>>(
+          Lh, Ll, ldf, k, R, ld, t, n, sc, d2h, d2l, part);
     else
-      ltr64_kernel<32><<<dim3(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 32)), 256, 0, ctx->stream>>>(
-          pc->L, pc->n, k, R, ld, t, n, sc, pc->dh64, part);
+      ltr_ff_kernel<32><<<dim3(nb, (unsigned)ceil_div(k, 64), (unsigned)ceil_div(t, 32)), 256, 0, ctx->stream>>>(
+          Lh, Ll, ldf, k, R, ld, t, n, sc, d2h, d2l, part);
     GP_LAUNCHED(ctx);
     const unsigned g2 = (unsigned)ceil_div((int64_t)k * t, 128);
     g_reduce_kernel<<<g2, 128, 0, ctx->stream>>>(part, nb, k, t, sc, G);
@@ -681,19 +733,17 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
     w64_apply_kernel<<<g2, 128, 0, ctx->stream>>>(pc->cinv, G, k, t, w64);
     GP_LAUNCHED(ctx);
     if (t <= 16) {
-      const size_t shm = sizeof(double) * (size_t)k * 16;
+      const size_t shm = sizeof(float) * 2 * (size_t)k * 16;
       if (shm > 48 * 1024)
-        GP_CUDA(ctx, cudaFuncSetAttribute(z64_apply_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)shm));
-      z64_apply_kernel<16><<<dim3(kRedBlocks, 1), 256, shm, ctx->stream>>>(pc->L, pc->n, k, w64, t, R, Z, ld, n,
-                                                                         pc->dh64, sc, rzpart);
+        GP_CUDA(ctx, cudaFuncSetAttribute(z_ff_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      z_ff_kernel<16><<<dim3(kRedBlocks, 1), 256, shm, ctx->stream>>>(Lh, Ll, ldf, k, w64, t, R, Z, ld, n, d2h,
+                                                                      d2l, sc, rzpart);
     } else {
-      const size_t shm = sizeof(double) * (size_t)k * 32;
+      const size_t shm = sizeof(float) * 2 * (size_t)k * 32;
       if (shm > 48 * 1024)
-        GP_CUDA(ctx, cudaFuncSetAttribute(z64_apply_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)shm));
-      z64_apply_kernel<32><<<dim3(kRedBlocks, (unsigned)ceil_div(t, 32)), 256, shm, ctx->stream>>>(
-          pc->L, pc->n, k, w64, t, R, Z, ld, n, pc->dh64, sc, rzpart);
+        GP_CUDA(ctx, cudaFuncSetAttribute(z_ff_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      z_ff_kernel<32><<<dim3(kRedBlocks, (unsigned)ceil_div(t, 32)), 256, shm, ctx->stream>>>(
+          Lh, Ll, ldf, k, w64, t, R, Z, ld, n, d2h, d2l, sc, rzpart);
     }
     GP_LAUNCHED(ctx);
     return GP_OK;

@@ -57,7 +57,7 @@ enum WsSlot {
   WS_PR_K, WS_PR_O, WS_STATUS, WS_PC_DG, WS_PC_DH, WS_PC_RES,
   WS_RF_R, WS_RF_D, WS_RF_W, WS_RF_S, WS_GT_P, WS_GT_T,
   WS_BC_C, WS_BC_P, WS_BC_W, WS_BC_S, WS_BC_R, WS_BC_RH, WS_BC_D, WS_BC_D2, WS_BC_DT,
-  WS_BC_WK, WS_BC_Q, WS_BC_OM, WS_BC_M, WS_BC_DH, WS_PC_DH64, WS_CG_W64,
+  WS_BC_WK, WS_BC_Q, WS_BC_OM, WS_BC_M, WS_BC_DH, WS_PC_D2FF, WS_PC_LFF, WS_CG_W64,
   WS_LV_W, WS_LV_P, WS_LV_T, WS_LV_K, WS_LV_M, WS_LV_C,
   WS_HO_IDX, WS_HO_X, WS_HO_Y,
   WS_HS_X, WS_HS_XP, WS_HS_V, WS_HS_O,
@@ -231,7 +231,8 @@ struct Precond {
   const double* resid = nullptr; // residual diagonal (device, nullable)
   const float* L32 = nullptr;    // L~ = D^{-1/2} L in FP32, ld n_pad
   const float* dh = nullptr;     // D^{-1/2}, n_pad floats (0 on padding)
-  const double* dh64 = nullptr;  // D^{-1/2} in FP64, n_pad (0 on padding)
+  const float* Lff = nullptr;    // the FP64 L as FP32 pairs: hi rows (rank x ld32), then lo rows
+  const float* d2ff = nullptr;   // D^{-1} as FP32 pairs: hi (ld32), then lo (ld32); 0 on padding
   int64_t ld32 = 0;
   const double* cfac = nullptr;  // k x k lower Cholesky of I + L~^T L~
   const double* cinv = nullptr;  // (I + L~^T L~)^{-1}, k x k, FP64

@@ -276,19 +276,39 @@ __global__ void pc_small_inverse(const double* __restrict__ F, int k,
 }
 
 // D_a = (resid_a or 0) + sigma2 (FP64), dh_a = D_a^{-1/2} (FP32, 0 on padding)
+// L (FP64, row j contiguous, ld n) as FP32 pairs: Lff[j ld32 + a] = hi =
+// fl32(L), Lff[(rank + j) ld32 + a] = fl32(L - hi); 0 on the padding rows
+__global__ void pc_split_ff_kernel(const double* __restrict__ L, int64_t n, int rank, int64_t ld32,
+                                   float* __restrict__ Lff) {
+  const int64_t total = (int64_t)rank * ld32;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx / ld32, a = idx % ld32;
+    const double v = a < n ? L[j * n + a] : 0.0;
+    const float vh = (float)v;
+    Lff[idx] = vh;
+    Lff[total + idx] = (float)(v - (double)vh);
+  }
+}
+
 __global__ void pc_diag_kernel(const double* __restrict__ resid, double sigma2, int64_t n,
                                int64_t ld32, double* __restrict__ Dg, float* __restrict__ dh,
-                               double* __restrict__ dh64) {
+                               float* __restrict__ d2ff) {
   for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < ld32;
        a += (int64_t)gridDim.x * blockDim.x) {
     if (a < n) {
       const double D = (resid ? resid[a] : 0.0) + sigma2;
       Dg[a] = D;
-      dh64[a] = 1.0 / sqrt(D);
-      dh[a] = (float)dh64[a];
+      dh[a] = (float)(1.0 / sqrt(D));
+      // D^{-1} as an FP32 pair hi + lo (the Woodbury apply's float-float)
+      const double q = 1.0 / D;
+      const float qh = (float)q;
+      d2ff[a] = qh;
+      d2ff[ld32 + a] = (float)(q - (double)qh);
     } else {
       dh[a] = 0.f;
-      dh64[a] = 0.0;
+      d2ff[a] = 0.f;
+      d2ff[ld32 + a] = 0.f;
     }
   }
 }
@@ -378,16 +398,16 @@ int precond_setup(gp_ctx* ctx, const double* L, int64_t n, int k_alloc,
   (void)k_alloc;
   double* Dg = ws<double>(ctx, WS_PC_DG, (size_t)pc.ld32 + 512);
   float* dh = ws<float>(ctx, WS_PC_DH, (size_t)pc.ld32);
-  double* dh64 = ws<double>(ctx, WS_PC_DH64, (size_t)pc.ld32);
-  if (!Dg || !dh || !dh64) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner diagonal)");
+  float* d2ff = ws<float>(ctx, WS_PC_D2FF, (size_t)2 * pc.ld32);
+  if (!Dg || !dh || !d2ff) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner diagonal)");
   double* lpart = Dg + pc.ld32;   // 256 partial sums of log D
   const unsigned eg0 = (unsigned)std::min<int64_t>(ceil_div(pc.ld32, 256), 16LL * ctx->num_sms);
-  pc_diag_kernel<<<eg0, 256, 0, ctx->stream>>>(resid, sigma2, n, pc.ld32, Dg, dh, dh64);
+  pc_diag_kernel<<<eg0, 256, 0, ctx->stream>>>(resid, sigma2, n, pc.ld32, Dg, dh, d2ff);
   GP_LAUNCHED(ctx);
   pc_logd_partial<<<256, 256, 0, ctx->stream>>>(Dg, n, lpart);
   GP_LAUNCHED(ctx);
   pc.dh = dh;
-  pc.dh64 = dh64;
+  pc.d2ff = d2ff;
   double* cf = ws<double>(ctx, WS_PC_CF, (size_t)2 * std::max(rank, 1) * std::max(rank, 1) + 8);
   if (!cf) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner)");
   double* cinv = cf + (size_t)rank * rank;
@@ -396,6 +416,12 @@ int precond_setup(gp_ctx* ctx, const double* L, int64_t n, int k_alloc,
   GP_CUDA(ctx, cudaMemsetAsync(ld_dev, 0, 2 * sizeof(double), ctx->stream));
   if (rank > 0) {
     float* L32 = ws<float>(ctx, WS_PC_L32, (size_t)rank * pc.ld32);
+    float* Lff = ws<float>(ctx, WS_PC_LFF, (size_t)2 * rank * pc.ld32);
+    if (!Lff) return set_err(ctx, GP_ENOMEM, "workspace (preconditioner factor pairs)");
+    const unsigned egs = (unsigned)std::min<int64_t>(ceil_div((int64_t)rank * pc.ld32, 256), 16LL * ctx->num_sms);
+    pc_split_ff_kernel<<<egs, 256, 0, ctx->stream>>>(L, n, rank, pc.ld32, Lff);
+    GP_LAUNCHED(ctx);
+    pc.Lff = Lff;
     const int npairs = rank * (rank + 1) / 2;
     const int nblk = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(n, 4096)), 2 * ctx->num_sms);
     const int64_t rows_per_blk = ceil_div(n, nblk);
