@@ -359,10 +359,18 @@ __global__ void __launch_bounds__(256, NC == 16 ? 2 : 1) z_ff_kernel(
       acch[cc] = 0.f;
       accl[cc] = 0.f;
     }
+    // the next pivot row's pair is loaded while this one is used
+    float lh = Lh[a], ll = Ll[a];
     for (int j = 0; j < k; ++j) {
-      const float lh = Lh[(int64_t)j * ldl + a], ll = Ll[(int64_t)j * ldl + a];
+      float nh = 0.f, nl = 0.f;
+      if (j + 1 < k) {
+        nh = Lh[(int64_t)(j + 1) * ldl + a];
+        nl = Ll[(int64_t)(j + 1) * ldl + a];
+      }
 #pragma unroll
       for (int cc = 0; cc < NC; ++cc) ff_mac(acch[cc], accl[cc], lh, ll, swh[j * NC + cc], swl[j * NC + cc]);
+      lh = nh;
+      ll = nl;
     }
     const float qh = d2h[a], ql = d2l[a];
 #pragma unroll
@@ -732,19 +740,13 @@ static int precond_apply_impl(gp_ctx* ctx, const Precond* pc, int64_t n,
     GP_LAUNCHED(ctx);
     w64_apply_kernel<<<g2, 128, 0, ctx->stream>>>(pc->cinv, G, k, t, w64);
     GP_LAUNCHED(ctx);
-    if (t <= 16) {
-      const size_t shm = sizeof(float) * 2 * (size_t)k * 16;
-      if (shm > 48 * 1024)
-        GP_CUDA(ctx, cudaFuncSetAttribute(z_ff_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      z_ff_kernel<16><<<dim3(kRedBlocks, 1), 256, shm, ctx->stream>>>(Lh, Ll, ldf, k, w64, t, R, Z, ld, n, d2h,
-                                                                      d2l, sc, rzpart);
-    } else {
-      const size_t shm = sizeof(float) * 2 * (size_t)k * 32;
-      if (shm > 48 * 1024)
-        GP_CUDA(ctx, cudaFuncSetAttribute(z_ff_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      z_ff_kernel<32><<<dim3(kRedBlocks, (unsigned)ceil_div(t, 32)), 256, shm, ctx->stream>>>(
-          Lh, Ll, ldf, k, w64, t, R, Z, ld, n, d2h, d2l, sc, rzpart);
-    }
+    // 16 columns per grid row at every t: two blocks per SM (the 32-column
+    // form needs 228 registers a thread and runs one)
+    const size_t shm = sizeof(float) * 2 * (size_t)k * 16;
+    if (shm > 48 * 1024)
+      GP_CUDA(ctx, cudaFuncSetAttribute(z_ff_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    z_ff_kernel<16><<<dim3(kRedBlocks, (unsigned)ceil_div(t, 16)), 256, shm, ctx->stream>>>(
+        Lh, Ll, ldf, k, w64, t, R, Z, ld, n, d2h, d2l, sc, rzpart);
     GP_LAUNCHED(ctx);
     return GP_OK;
   }
